@@ -1,0 +1,701 @@
+// lbm_api.cu -- the C ABI of liblbm (declared in include/lbm.h): context
+// lifetime, device memory layout, tile tables, the launch-shape autotuner,
+// CUDA-graph replay of the step loop, and host I/O.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_aux.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int64_t ROW_ALIGN = 8;       // row pitch multiple (nodes)
+constexpr int64_t PLANE_ALIGN = 128;   // plane / instance alignment (elements)
+constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even)
+
+size_t dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
+
+struct Shape {
+    int V, tw, th;
+};
+
+// Launch-shape candidates.  V (nodes per thread) is limited to the compiled
+// widths of each storage type; tw is a power of two.
+std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, int64_t max_ny) {
+    std::vector<int> vs;
+    if (storage == DT_F64) vs = {2};
+    else if (storage == DT_F32) vs = {2, 4};
+    else vs = {4, 8};
+    std::vector<Shape> out;
+    for (int V : vs) {
+        for (int block : {128, 256}) {
+            for (int tw = 4; tw <= block; tw *= 2) {
+                const int th = block / tw;
+                if (lattice == 1 && th != 1) continue;
+                if (lattice == 2 && th > max_ny && tw < block) continue;
+                if ((int64_t)tw * V > 2 * std::max<int64_t>(max_nx, 8) && tw > 4) continue;
+                out.push_back({V, tw, th});
+            }
+        }
+    }
+    return out;
+}
+
+Shape default_shape(int lattice, int storage) {
+    if (lattice == 1) return {storage == DT_F64 ? 2 : 4, 128, 1};
+    if (storage == DT_F64) return {2, 16, 8};
+    if (storage == DT_F32) return {4, 16, 8};
+    return {8, 8, 16};
+}
+
+int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const Shape& s) {
+    int64_t n = 0;
+    for (auto& d : dims) {
+        const int64_t chunks = (d.first + s.V - 1) / s.V;
+        n += ((chunks + s.tw - 1) / s.tw) * ((d.second + s.th - 1) / s.th);
+    }
+    return n;
+}
+
+struct Layout {
+    std::vector<InstDesc> inst;
+    int64_t elems = 0;       // elements per population buffer
+    int64_t total_nodes = 0;
+    int64_t max_nodes = 0, max_nx = 0, max_ny = 0;
+    int64_t max_tiles = 0;
+};
+
+Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t, int64_t>>& dims) {
+    Layout L;
+    const int Q = lattice == 2 ? 9 : 3;
+    int64_t off = 0, node0 = 0;
+    for (auto& d : dims) {
+        InstDesc in;
+        std::memset(&in, 0, sizeof in);
+        in.nx = (int32_t)d.first;
+        in.ny = (int32_t)d.second;
+        in.pitch = (int32_t)round_up(d.first, ROW_ALIGN);
+        in.plane = round_up((int64_t)in.pitch * in.ny, PLANE_ALIGN);
+        in.off = off;
+        in.node0 = node0;
+        off += Q * in.plane;
+        node0 += d.first * d.second;
+        L.max_nodes = std::max(L.max_nodes, d.first * d.second);
+        L.max_nx = std::max(L.max_nx, d.first);
+        L.max_ny = std::max(L.max_ny, d.second);
+        L.inst.push_back(in);
+    }
+    L.elems = off;
+    L.total_nodes = node0;
+    for (const Shape& s : candidate_shapes(lattice, storage, L.max_nx, L.max_ny))
+        L.max_tiles = std::max(L.max_tiles, count_tiles(dims, s));
+    L.max_tiles = std::max(L.max_tiles, count_tiles(dims, default_shape(lattice, storage)));
+    return L;
+}
+
+struct Carve {
+    size_t buf_bytes, inst_off, tiles_off, status_off, partials_off, stage_off, total;
+};
+
+Carve carve(const Layout& L, int lattice, int storage, int count) {
+    const int Q = lattice == 2 ? 9 : 3;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    Carve c;
+    c.buf_bytes = al((size_t)L.elems * dtype_bytes(storage));
+    size_t p = 2 * c.buf_bytes;
+    c.inst_off = p;
+    p += al(sizeof(InstDesc) * count);
+    c.tiles_off = p;
+    p += al(sizeof(TileDesc) * (size_t)std::max<int64_t>(L.max_tiles, 1));
+    c.status_off = p;
+    p += al(sizeof(unsigned long long) * 2 * count);
+    c.partials_off = p;
+    p += al(sizeof(double) * 3 * (size_t)CONS_PARTIALS * count);
+    c.stage_off = p;
+    p += al(sizeof(double) * std::max<int64_t>(3 * L.total_nodes, Q * L.total_nodes));
+    c.total = p;
+    return c;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    int lattice = 2, Q = 9, count = 0, bc = 0, compute = DT_F64, storage = DT_F64;
+    int collision = COLL_MINXENT4;
+    double rho0 = 1.0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int num_sms = 0;
+    bool own_mem = false;
+    char* mem = nullptr;
+    Layout layout;
+    Carve cv{};
+    char* buf[2] = {nullptr, nullptr};
+    int cur = 0;  // buffer holding the current state
+    InstDesc* d_inst = nullptr;
+    TileDesc* d_tiles = nullptr;
+    unsigned long long* d_status = nullptr;
+    double* d_partials = nullptr;
+    double* d_stage = nullptr;
+    std::vector<TileDesc> tiles;
+    bool initialized = false;
+    bool post = false;  // stored field is post-collision
+    int64_t steps = 0;
+    Shape shape{};
+    const void* kern = nullptr;
+    int grid = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool failed = false;
+};
+
+namespace {
+
+#define LBM_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            if (getenv("LBM_DEBUG"))                                                   \
+                fprintf(stderr, "liblbm: %s failed: %s (%s:%d)\n", #call,              \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+            if (ctx) ctx->failed = true;                                               \
+            return LBM_ERR_CUDA;                                                       \
+        }                                                                              \
+    } while (0)
+
+const void* find_step_kernel(int lattice, int storage, int collision, int V) {
+    switch (storage) {
+        case DT_F64: return step_kernel_f64(lattice, collision, V);
+        case DT_F32: return step_kernel_f32(lattice, collision, V);
+        case DT_F16: return step_kernel_f16(lattice, collision, V);
+        case DT_BF16: return step_kernel_bf16(lattice, collision, V);
+    }
+    return nullptr;
+}
+
+AuxArgs aux_args(const lbm_ctx* ctx) {
+    AuxArgs a;
+    a.lattice = ctx->lattice;
+    a.storage = ctx->storage;
+    a.compute = ctx->compute;
+    a.collision = ctx->collision;
+    a.count = ctx->count;
+    a.max_nodes = ctx->layout.max_nodes;
+    a.inst = ctx->d_inst;
+    a.rho0 = ctx->rho0;
+    a.pulled = ctx->post;
+    a.status = ctx->d_status;
+    a.stream = ctx->stream;
+    return a;
+}
+
+std::vector<TileDesc> build_tiles(const lbm_ctx* ctx, const Shape& s) {
+    std::vector<TileDesc> t;
+    for (int i = 0; i < ctx->count; ++i) {
+        const InstDesc& in = ctx->layout.inst[i];
+        const int64_t chunks = (in.nx + s.V - 1) / s.V;
+        for (int64_t y0 = 0; y0 < in.ny; y0 += s.th)
+            for (int64_t c0 = 0; c0 < chunks; c0 += s.tw)
+                t.push_back({(int32_t)i, (int32_t)c0, (int32_t)y0, 0});
+    }
+    return t;
+}
+
+int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+// Make shape s current: tile table to the device, kernel and grid size.
+int apply_shape(lbm_ctx* ctx, const Shape& s) {
+    const void* k = find_step_kernel(ctx->lattice, ctx->storage, ctx->collision, s.V);
+    if (!k) return LBM_ERR_ARG;
+    std::vector<TileDesc> t = build_tiles(ctx, s);
+    if ((int64_t)t.size() > ctx->layout.max_tiles) return LBM_ERR_ARG;
+    // the instance table records each instance's tile range
+    int32_t idx = 0;
+    for (int i = 0; i < ctx->count; ++i) {
+        ctx->layout.inst[i].tile0 = idx;
+        int32_t n = 0;
+        while (idx + n < (int32_t)t.size() && t[idx + n].inst == i) ++n;
+        ctx->layout.inst[i].ntiles = n;
+        idx += n;
+    }
+    LBM_CK(cudaMemcpyAsync(ctx->d_tiles, t.data(), sizeof(TileDesc) * t.size(),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    LBM_CK(cudaMemcpyAsync(ctx->d_inst, ctx->layout.inst.data(), sizeof(InstDesc) * ctx->count,
+                           cudaMemcpyHostToDevice, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    const int block = s.tw * s.th;
+    int per_sm = 0;
+    LBM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0));
+    per_sm = std::max(per_sm, 1);
+    const int64_t g = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, (int64_t)t.size());
+    ctx->tiles.swap(t);
+    ctx->shape = s;
+    ctx->kern = k;
+    ctx->grid = (int)std::max<int64_t>(g, 1);
+    for (int p = 0; p < 2; ++p) {
+        if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
+        ctx->graph[p] = nullptr;
+    }
+    return LBM_OK;
+}
+
+StepArgs step_args(const lbm_ctx* ctx, int src) {
+    StepArgs a;
+    a.src = ctx->buf[src];
+    a.dst = ctx->buf[1 - src];
+    a.inst = ctx->d_inst;
+    a.tiles = ctx->d_tiles;
+    a.ntiles = (int32_t)ctx->tiles.size();
+    a.tw = ctx->shape.tw;
+    a.tw_log2 = ilog2(ctx->shape.tw);
+    a.th = ctx->shape.th;
+    a.rho0 = ctx->rho0;
+    a.status = ctx->d_status;
+    return a;
+}
+
+cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
+    StepArgs a = step_args(ctx, src);
+    void* params[] = {&a};
+    return cudaLaunchKernel(ctx->kern, dim3(ctx->grid), dim3(ctx->shape.tw * ctx->shape.th),
+                            params, 0, s);
+}
+
+// Time candidate shapes on the zeroed (rest-state) buffers and keep the fastest.
+int autotune(lbm_ctx* ctx) {
+    std::vector<Shape> cands = candidate_shapes(ctx->lattice, ctx->storage, ctx->layout.max_nx,
+                                                ctx->layout.max_ny);
+    cudaEvent_t e0, e1;
+    LBM_CK(cudaEventCreate(&e0));
+    LBM_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Shape best_s = default_shape(ctx->lattice, ctx->storage);
+    const int reps = ctx->layout.total_nodes > (1 << 22) ? 4 : 12;
+    for (const Shape& s : cands) {
+        if (apply_shape(ctx, s) != LBM_OK) continue;
+        for (int w = 0; w < 2; ++w) LBM_CK(launch_step(ctx, w & 1, ctx->stream));
+        LBM_CK(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < reps; ++r) LBM_CK(launch_step(ctx, r & 1, ctx->stream));
+        LBM_CK(cudaEventRecord(e1, ctx->stream));
+        LBM_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LBM_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_s = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // undo the tuning steps: back to the rest state, counters cleared
+    LBM_CK(cudaMemsetAsync(ctx->buf[0], 0, 2 * ctx->cv.buf_bytes, ctx->stream));
+    LBM_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned long long) * 2 * ctx->count,
+                           ctx->stream));
+    return apply_shape(ctx, best_s);
+}
+
+bool parse_shape_env(Shape* s) {
+    const char* e = getenv("LBM_SHAPE");
+    if (!e) return false;
+    int v, tw, th;
+    if (sscanf(e, "%d,%d,%d", &v, &tw, &th) != 3) return false;
+    *s = {v, tw, th};
+    return true;
+}
+
+void lid_deviation(double rho0, double u, double* dev) {
+    // f^eq_a(rho0, (u, 0)) - W_a rho0, Eq. (numerical-plyeqm); D2Q9 in T's column order.
+    static const int vx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    for (int a = 0; a < 9; ++a) {
+        const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        const double vu = vx[a] * u;
+        dev[a] = w * rho0 * (3.0 * vu + 4.5 * vu * vu - 1.5 * u * u);
+    }
+}
+
+int validate_opts(const lbm_opts* o) {
+    if (o->compute != DT_F64 && o->compute != DT_F32) return LBM_ERR_ARG;
+    if (o->storage < DT_F64 || o->storage > DT_BF16) return LBM_ERR_ARG;
+    if (o->compute == DT_F64 && o->storage != DT_F64) return LBM_ERR_ARG;
+    if (o->compute == DT_F32 && o->storage == DT_F64) return LBM_ERR_ARG;
+    if (o->collision != COLL_MINXENT4 && o->collision != COLL_SRT) return LBM_ERR_ARG;
+    if (!(o->rho0 > 0.0) || !std::isfinite(o->rho0)) return LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+int validate_dims(int lat, int32_t count, const int64_t* dims,
+                  std::vector<std::pair<int64_t, int64_t>>* out) {
+    if (lat != 1 && lat != 2) return LBM_ERR_ARG;
+    if (count < 1 || count > 65535 || !dims) return LBM_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        const int64_t nx = dims[2 * i], ny = dims[2 * i + 1];
+        if (nx < 1 || ny < 1 || nx > (1 << 26) || ny > (1 << 26)) return LBM_ERR_ARG;
+        if (lat == 1 && ny != 1) return LBM_ERR_ARG;
+        if (nx * ny > ((int64_t)1 << 31)) return LBM_ERR_ARG;
+        out->push_back({nx, ny});
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->compute = DT_F64;
+    o->storage = DT_F64;
+    o->collision = COLL_MINXENT4;
+    o->autotune = 1;
+    o->rho0 = 1.0;
+}
+
+int lbm_required_bytes(lbm_lattice lat, int32_t count, const int64_t* dims, const lbm_opts* opts,
+                       uint64_t* bytes) {
+    if (!bytes) return LBM_ERR_ARG;
+    lbm_opts o;
+    if (opts) o = *opts;
+    else lbm_default_opts(&o);
+    if (validate_opts(&o) != LBM_OK) return LBM_ERR_ARG;
+    std::vector<std::pair<int64_t, int64_t>> d;
+    if (validate_dims(lat, count, dims, &d) != LBM_OK) return LBM_ERR_ARG;
+    Layout L = make_layout(lat, o.storage, d);
+    *bytes = carve(L, lat, o.storage, count).total;
+    return LBM_OK;
+}
+
+int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_t* dims,
+                     const double* nu, const double* u_lid, lbm_bc bc, const lbm_opts* opts) {
+    lbm_ctx* ctx = nullptr;
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_opts o;
+    if (opts) o = *opts;
+    else lbm_default_opts(&o);
+    if (validate_opts(&o) != LBM_OK) return LBM_ERR_ARG;
+    std::vector<std::pair<int64_t, int64_t>> d;
+    if (validate_dims(lat, count, dims, &d) != LBM_OK || !nu) return LBM_ERR_ARG;
+    if (bc != LBM_BC_PERIODIC && bc != LBM_BC_ZERO_GRADIENT && bc != LBM_BC_CAVITY)
+        return LBM_ERR_ARG;
+    if (bc == LBM_BC_CAVITY) {
+        if (lat != LBM_D2Q9) return LBM_ERR_ARG;
+        for (auto& p : d)
+            if (p.first < 3 || p.second < 3) return LBM_ERR_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        // Eq. (visco-tau): tau = 3 nu + 1/2 must exceed 1/2
+        if (!(nu[i] > 0.0) || !std::isfinite(nu[i])) return LBM_ERR_ARG;
+        if (u_lid && !std::isfinite(u_lid[i])) return LBM_ERR_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_NODEV;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return LBM_ERR_NODEV;
+    if (prop.major != 10 || prop.minor != 3) return LBM_ERR_NODEV;
+
+    ctx = new lbm_ctx();
+    ctx->lattice = lat;
+    ctx->Q = lat == LBM_D2Q9 ? 9 : 3;
+    ctx->count = count;
+    ctx->bc = bc;
+    ctx->compute = o.compute;
+    ctx->storage = o.storage;
+    ctx->collision = o.collision;
+    ctx->rho0 = o.rho0;
+    ctx->stream = static_cast<cudaStream_t>(o.stream);
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->layout = make_layout(lat, o.storage, d);
+    ctx->cv = carve(ctx->layout, lat, o.storage, count);
+    for (int i = 0; i < count; ++i) {
+        InstDesc& in = ctx->layout.inst[i];
+        const double tau = 3.0 * nu[i] + 0.5;
+        in.bc = bc;
+        in.omega = 1.0 / tau;
+        in.u_lid = u_lid ? u_lid[i] : 0.0;
+        if (bc == LBM_BC_CAVITY) {
+            lid_deviation(o.rho0, in.u_lid, in.lid_dev);
+            for (int a = 0; a < 9; ++a) in.lid_dev_f[a] = (float)in.lid_dev[a];
+        }
+    }
+    int rc = LBM_OK;
+    if (o.device_mem) {
+        if (o.device_mem_bytes < ctx->cv.total || ((uintptr_t)o.device_mem & 255u)) {
+            delete ctx;
+            return LBM_ERR_ARG;
+        }
+        ctx->mem = static_cast<char*>(o.device_mem);
+    } else {
+        void* p = nullptr;
+        if (cudaMalloc(&p, ctx->cv.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return LBM_ERR_ALLOC;
+        }
+        ctx->mem = static_cast<char*>(p);
+        ctx->own_mem = true;
+    }
+    ctx->buf[0] = ctx->mem;
+    ctx->buf[1] = ctx->mem + ctx->cv.buf_bytes;
+    ctx->d_inst = reinterpret_cast<InstDesc*>(ctx->mem + ctx->cv.inst_off);
+    ctx->d_tiles = reinterpret_cast<TileDesc*>(ctx->mem + ctx->cv.tiles_off);
+    ctx->d_status = reinterpret_cast<unsigned long long*>(ctx->mem + ctx->cv.status_off);
+    ctx->d_partials = reinterpret_cast<double*>(ctx->mem + ctx->cv.partials_off);
+    ctx->d_stage = reinterpret_cast<double*>(ctx->mem + ctx->cv.stage_off);
+    auto fail = [&](int code) {
+        lbm_destroy(ctx);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(LBM_ERR_CUDA);
+    if (cudaMemsetAsync(ctx->mem, 0, ctx->cv.total, ctx->stream) != cudaSuccess)
+        return fail(LBM_ERR_CUDA);
+    Shape s;
+    if (parse_shape_env(&s)) rc = apply_shape(ctx, s);
+    else if (o.autotune && !getenv("LBM_NO_AUTOTUNE")) rc = autotune(ctx);
+    else rc = apply_shape(ctx, default_shape(lat, o.storage));
+    if (rc != LBM_OK) return fail(rc);
+    *out = ctx;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_ctx** out, lbm_lattice lat, const int64_t* dims, double nu, lbm_bc bc,
+               double u_lid, const lbm_opts* opts) {
+    return lbm_create_batch(out, lat, 1, dims, &nu, &u_lid, bc, opts);
+}
+
+int lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return LBM_OK;
+    for (int p = 0; p < 2; ++p)
+        if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->own_mem && ctx->mem) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->mem);
+    }
+    delete ctx;
+    return LBM_OK;
+}
+
+int lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy) {
+    if (!ctx || !rho) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    AuxArgs a = aux_args(ctx);
+    LBM_CK(run_aux(AuxOp::Init, a, nullptr, ctx->buf[ctx->cur], rho, ux, uy, nullptr, nullptr,
+                   nullptr));
+    LBM_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned long long) * 2 * ctx->count,
+                           ctx->stream));
+    ctx->post = false;
+    ctx->initialized = true;
+    ctx->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy) {
+    if (!ctx || !rho) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    const size_t n = (size_t)ctx->layout.total_nodes;
+    double* r = ctx->d_stage;
+    double* x = ux ? ctx->d_stage + n : nullptr;
+    double* y = (uy && ctx->Q == 9) ? ctx->d_stage + 2 * n : nullptr;
+    LBM_CK(cudaMemcpyAsync(r, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (x) LBM_CK(cudaMemcpyAsync(x, ux, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (y) LBM_CK(cudaMemcpyAsync(y, uy, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    int rc = lbm_init_device(ctx, r, x, y);
+    if (rc != LBM_OK) return rc;
+    // the caller may reuse its arrays once we return
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* ctx, int64_t n) {
+    if (!ctx || n < 0) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (n == 0) return LBM_OK;
+    if (!ctx->post) {
+        AuxArgs a = aux_args(ctx);
+        LBM_CK(run_aux(AuxOp::CollideInPlace, a, ctx->buf[ctx->cur], ctx->buf[1 - ctx->cur],
+                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
+        ctx->cur = 1 - ctx->cur;
+        ctx->post = true;
+        ctx->steps += 1;
+        --n;
+    }
+    while (n >= GRAPH_STEPS) {
+        cudaGraphExec_t& g = ctx->graph[ctx->cur];
+        if (!g) {
+            cudaGraph_t graph;
+            LBM_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+            int src = ctx->cur;
+            for (int k = 0; k < GRAPH_STEPS; ++k) {
+                cudaError_t e = launch_step(ctx, src, ctx->capture_stream);
+                if (e != cudaSuccess) {
+                    cudaStreamEndCapture(ctx->capture_stream, &graph);
+                    LBM_CK(e);
+                }
+                src = 1 - src;
+            }
+            LBM_CK(cudaStreamEndCapture(ctx->capture_stream, &graph));
+            cudaError_t e = cudaGraphInstantiate(&g, graph, 0);
+            cudaGraphDestroy(graph);
+            LBM_CK(e);
+        }
+        LBM_CK(cudaGraphLaunch(g, ctx->stream));
+        n -= GRAPH_STEPS;
+        ctx->steps += GRAPH_STEPS;
+    }
+    for (; n > 0; --n) {
+        LBM_CK(launch_step(ctx, ctx->cur, ctx->stream));
+        ctx->cur = 1 - ctx->cur;
+        ctx->steps += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments_device(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
+    if (!ctx || !rho) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    AuxArgs a = aux_args(ctx);
+    LBM_CK(run_aux(AuxOp::Moments, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr, rho,
+                   ux, ctx->Q == 9 ? uy : nullptr));
+    return LBM_OK;
+}
+
+int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters) {
+    if (!ctx || !counters || instance < 0 || instance >= ctx->count) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    unsigned long long h[2];
+    LBM_CK(cudaMemcpyAsync(h, ctx->d_status + 2 * instance, sizeof h, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    counters[0] = (int64_t)h[0];
+    counters[1] = (int64_t)h[1];
+    counters[2] = ctx->steps;
+    return LBM_OK;
+}
+
+int lbm_status(lbm_ctx* ctx, int64_t* counters) {
+    if (!ctx || !counters) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    std::vector<unsigned long long> h(2 * (size_t)ctx->count);
+    LBM_CK(cudaMemcpyAsync(h.data(), ctx->d_status, sizeof(unsigned long long) * h.size(),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    counters[0] = counters[1] = 0;
+    for (int i = 0; i < ctx->count; ++i) {
+        counters[0] += (int64_t)h[2 * i];
+        counters[1] += (int64_t)h[2 * i + 1];
+    }
+    counters[2] = ctx->steps;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
+    if (!ctx || !rho) return LBM_ERR_ARG;
+    const size_t n = (size_t)ctx->layout.total_nodes;
+    double* r = ctx->d_stage;
+    double* x = ctx->d_stage + n;
+    double* y = ctx->d_stage + 2 * n;
+    int rc = lbm_moments_device(ctx, r, x, y);
+    if (rc != LBM_OK) return rc;
+    LBM_CK(cudaMemcpyAsync(rho, r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ux) LBM_CK(cudaMemcpyAsync(ux, x, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (uy && ctx->Q == 9)
+        LBM_CK(cudaMemcpyAsync(uy, y, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    int64_t c[3];
+    rc = lbm_status(ctx, c);
+    if (rc != LBM_OK) return rc;
+    return c[1] ? LBM_ERR_UNSTABLE : LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* ctx, double* f) {
+    if (!ctx || !f) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    const size_t n = (size_t)ctx->layout.total_nodes * ctx->Q;
+    AuxArgs a = aux_args(ctx);
+    LBM_CK(run_aux(AuxOp::GatherF, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr,
+                   ctx->d_stage, nullptr, nullptr));
+    LBM_CK(cudaMemcpyAsync(f, ctx->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* ctx, const double* f) {
+    if (!ctx || !f) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    const size_t n = (size_t)ctx->layout.total_nodes * ctx->Q;
+    LBM_CK(cudaMemcpyAsync(ctx->d_stage, f, n * sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    AuxArgs a = aux_args(ctx);
+    LBM_CK(run_aux(AuxOp::SetF, a, nullptr, ctx->buf[ctx->cur], ctx->d_stage, nullptr, nullptr,
+                   nullptr, nullptr, nullptr));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->post = false;
+    ctx->initialized = true;
+    return LBM_OK;
+}
+
+int lbm_conservation(lbm_ctx* ctx, double* out) {
+    if (!ctx || !out) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    AuxArgs a = aux_args(ctx);
+    LBM_CK(run_aux(AuxOp::Conservation, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr,
+                   ctx->d_stage, ctx->d_partials, nullptr));
+    LBM_CK(cudaMemcpyAsync(out, ctx->d_stage, sizeof(double) * 3 * ctx->count,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+int lbm_conservation_device(lbm_ctx* ctx, double* out) {
+    if (!ctx || !out) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    AuxArgs a = aux_args(ctx);
+    LBM_CK(run_aux(AuxOp::Conservation, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr,
+                   out, ctx->d_partials, nullptr));
+    return LBM_OK;
+}
+
+int lbm_launch_shape(lbm_ctx* ctx, int32_t* out) {
+    if (!ctx || !out) return LBM_ERR_ARG;
+    out[0] = ctx->shape.V;
+    out[1] = ctx->shape.tw;
+    out[2] = ctx->shape.th;
+    out[3] = ctx->grid;
+    return LBM_OK;
+}
+
+const char* lbm_status_string(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_ALLOC: return "device memory allocation failed";
+        case LBM_ERR_CUDA: return "CUDA runtime error";
+        case LBM_ERR_UNSTABLE: return "unstable: negative or non-finite population";
+        case LBM_ERR_STATE: return "call out of order (context not initialised)";
+        case LBM_ERR_NODEV: return "no sm_103 CUDA device";
+    }
+    return "unknown status code";
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// lbm_aux.cu -- the kernels around the time step: initial equilibrium,
+// the first (in-place) collision after a state is loaded, moments and
+// population read-out, population load, and the FP64 conservation
+// reduction.  One thread per node, grid = (blocks, instance); none of these
+// is on the per-step hot path.
+#include "lbm_aux.h"
+#include "lbm_collide.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int AUX_THREADS = 256;
+
+template <class Lat, typename S>
+__device__ __forceinline__ const S* elem_ptr(const S* base, const InstDesc& in, int a, int x, int y) {
+    return base + in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x;
+}
+
+// Deviations of f(x, t_n) at one node, FP64.  pulled = true: the stored field
+// is post-collision and the node pulls f_a from x - v_a with the boundary
+// rules of the step; pulled = false: the stored field is f(x, t_n) itself.
+template <class Lat, typename S>
+__device__ void node_state(const S* base, const InstDesc& in, int x, int y, bool pulled,
+                           double (&d)[Lat::Q]) {
+#pragma unroll
+    for (int a = 0; a < Lat::Q; ++a) {
+        int sx = x, sy = y;
+        bool inside = true;
+        if (pulled) {
+            sx = x - Lat::vx(a);
+            sy = y - Lat::vy(a);
+            if (in.bc == BC_CAVITY) {
+                inside = sx >= 0 && sx < in.nx && sy >= 0 && sy < in.ny;
+            } else {
+                if (in.bc == BC_PERIODIC) sx = (sx + in.nx) % in.nx;
+                else sx = sx < 0 ? 0 : (sx >= in.nx ? in.nx - 1 : sx);
+                sy = (sy + in.ny) % in.ny;
+            }
+        }
+        d[a] = inside ? Store<S>::to_f64(*elem_ptr<Lat, S>(base, in, a, sx, sy)) : 0.0;
+    }
+}
+
+// f^eq(rho, u) - W rho0 in FP64 (Eq. numerical-plyeqm).
+template <class Lat>
+__device__ void eq_dev(double rho, double ux, double uy, double rho0, double (&d)[Lat::Q]) {
+    const double uu = ux * ux + uy * uy;
+#pragma unroll
+    for (int a = 0; a < Lat::Q; ++a) {
+        const double vu = Lat::vx(a) * ux + Lat::vy(a) * uy;
+        d[a] = Lat::w(a) * (rho - rho0) + Lat::w(a) * rho * (3.0 * vu + 4.5 * vu * vu - 1.5 * uu);
+    }
+}
+
+template <class Lat, typename S>
+__global__ void init_kernel(S* dst, const InstDesc* insts, const double* rho, const double* ux,
+                            const double* uy, double rho0) {
+    const InstDesc in = insts[blockIdx.y];
+    const int64_t n = (int64_t)in.nx * in.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+        const int64_t g = in.node0 + k;
+        double d[Lat::Q];
+        eq_dev<Lat>(rho[g], ux ? ux[g] : 0.0, (uy && Lat::Q == 9) ? uy[g] : 0.0, rho0, d);
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a)
+            dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(d[a]);
+    }
+}
+
+template <class Lat, typename S>
+__global__ void set_f_kernel(S* dst, const InstDesc* insts, const double* f, double rho0) {
+    const InstDesc in = insts[blockIdx.y];
+    const int64_t n = (int64_t)in.nx * in.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a) {
+            const double fa = f[in.node0 * Lat::Q + (int64_t)a * n + k];
+            dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] =
+                Store<S>::from(fa - Lat::w(a) * rho0);
+        }
+    }
+}
+
+// First step after a state was loaded: collide in place, no streaming
+// (the loaded field is f(x, t_n) itself, Eq. 2's collision input).
+template <class Lat, typename S, typename T, int COLL>
+__global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* insts, double rho0,
+                                       unsigned long long* status) {
+    const int inst = blockIdx.y;
+    const InstDesc& in = insts[inst];
+    const int64_t n = (int64_t)in.nx * in.ny;
+    unsigned long long n_skip = 0, n_unst = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+        T d[Lat::Q], o[Lat::Q];
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a) {
+            const S v = *elem_ptr<Lat, S>(src, in, a, x, y);
+            if constexpr (std::is_same<T, double>::value) d[a] = Store<S>::to_f64(v);
+            else d[a] = Store<S>::to_f32(v);
+        }
+        uint32_t st = Collide<Lat, COLL, T>::run(d, (T)rho0, (T)in.omega, o);
+        if (in.bc == BC_CAVITY) {
+            const bool wall = (x == 0) || (x == in.nx - 1) || (y == 0);
+            const bool lid = !wall && (y == in.ny - 1);
+            if (wall) {
+#pragma unroll
+                for (int a = 0; a < Lat::Q; ++a) o[a] = d[Lat::opp(a)];
+                st = 0;
+            } else if (lid) {
+#pragma unroll
+                for (int a = 0; a < Lat::Q; ++a)
+                    o[a] = std::is_same<T, double>::value ? (T)in.lid_dev[a] : (T)in.lid_dev_f[a];
+                st = 0;
+            }
+        }
+        n_skip += st & ST_NEWTON_SKIPPED;
+        n_unst += (st & ST_UNSTABLE) >> 1;
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a)
+            dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(o[a]);
+    }
+    if (n_skip) atomicAdd(status + 2 * inst + 0, n_skip);
+    if (n_unst) atomicAdd(status + 2 * inst + 1, n_unst);
+}
+
+template <class Lat, typename S>
+__global__ void moments_kernel(const S* src, const InstDesc* insts, bool pulled, double rho0,
+                               double* rho, double* ux, double* uy) {
+    const InstDesc in = insts[blockIdx.y];
+    const int64_t n = (int64_t)in.nx * in.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+        double d[Lat::Q];
+        node_state<Lat, S>(src, in, x, y, pulled, d);
+        double dr = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a) {
+            dr += d[a];
+            jx += Lat::vx(a) * d[a];
+            jy += Lat::vy(a) * d[a];
+        }
+        const double r = rho0 + dr;
+        const int64_t g = in.node0 + k;
+        rho[g] = r;
+        if (ux) ux[g] = jx / r;
+        if (uy) uy[g] = jy / r;
+    }
+}
+
+template <class Lat, typename S>
+__global__ void gather_f_kernel(const S* src, const InstDesc* insts, bool pulled, double rho0,
+                                double* f) {
+    const InstDesc in = insts[blockIdx.y];
+    const int64_t n = (int64_t)in.nx * in.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+        double d[Lat::Q];
+        node_state<Lat, S>(src, in, x, y, pulled, d);
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a)
+            f[in.node0 * Lat::Q + (int64_t)a * n + k] = Lat::w(a) * rho0 + d[a];
+    }
+}
+
+// Conservation, pass 1: block b of instance i sums (sum d, sum d v_x,
+// sum d v_y) over nodes k = b*256 + t + j*P*256 in FP64 and reduces the
+// block in a fixed tree; partials[(i*P + b)*3 + c].  The grid (P blocks per
+// instance) is a constant, so the summation order is fixed.
+template <class Lat, typename S>
+__global__ void __launch_bounds__(AUX_THREADS)
+cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* partials) {
+    __shared__ double sh[3][AUX_THREADS];
+    const InstDesc in = insts[blockIdx.y];
+    const int64_t n = (int64_t)in.nx * in.ny;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * AUX_THREADS + threadIdx.x; k < n;
+         k += (int64_t)CONS_PARTIALS * AUX_THREADS) {
+        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+        double d[Lat::Q];
+        node_state<Lat, S>(src, in, x, y, pulled, d);
+#pragma unroll
+        for (int a = 0; a < Lat::Q; ++a) {
+            s0 += d[a];
+            s1 += Lat::vx(a) * d[a];
+            s2 += Lat::vy(a) * d[a];
+        }
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    sh[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int h = AUX_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 3)
+        partials[((int64_t)blockIdx.y * CONS_PARTIALS + blockIdx.x) * 3 + threadIdx.x] =
+            sh[threadIdx.x][0];
+}
+
+// Conservation, pass 2: one thread per instance adds its partials in order;
+// total mass = N rho0 + sum d (sum_a W_a = 1).
+__global__ void cons_final_kernel(const double* partials, const InstDesc* insts, int count,
+                                  double rho0, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < CONS_PARTIALS; ++b)
+        for (int c = 0; c < 3; ++c) s[c] += partials[((int64_t)i * CONS_PARTIALS + b) * 3 + c];
+    const double nodes = (double)insts[i].nx * (double)insts[i].ny;
+    out[3 * i + 0] = nodes * rho0 + s[0];
+    out[3 * i + 1] = s[1];
+    out[3 * i + 2] = s[2];
+}
+
+dim3 aux_grid(int64_t max_nodes, int count) {
+    int64_t b = (max_nodes + AUX_THREADS - 1) / AUX_THREADS;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return dim3((unsigned)b, (unsigned)count);
+}
+
+template <class Lat, typename S, typename T, int COLL>
+cudaError_t collide_inplace_dispatch(const AuxArgs& a, const void* src, void* dst) {
+    collide_inplace_kernel<Lat, S, T, COLL><<<aux_grid(a.max_nodes, a.count), AUX_THREADS, 0, a.stream>>>(
+        static_cast<const S*>(src), static_cast<S*>(dst), a.inst, a.rho0, a.status);
+    return cudaGetLastError();
+}
+
+template <class Lat, typename S>
+cudaError_t aux_dispatch(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
+                         const double* p1, const double* p2, double* o0, double* o1, double* o2) {
+    const dim3 g = aux_grid(a.max_nodes, a.count);
+    switch (op) {
+        case AuxOp::Init:
+            init_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<S*>(dst), a.inst, p0, p1,
+                                                                 p2, a.rho0);
+            break;
+        case AuxOp::SetF:
+            set_f_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<S*>(dst), a.inst, p0,
+                                                                  a.rho0);
+            break;
+        case AuxOp::Moments:
+            moments_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<const S*>(src), a.inst,
+                                                                    a.pulled, a.rho0, o0, o1, o2);
+            break;
+        case AuxOp::GatherF:
+            gather_f_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<const S*>(src),
+                                                                     a.inst, a.pulled, a.rho0, o0);
+            break;
+        case AuxOp::Conservation: {
+            cons_partial_kernel<Lat, S><<<dim3(CONS_PARTIALS, a.count), AUX_THREADS, 0, a.stream>>>(
+                static_cast<const S*>(src), a.inst, a.pulled, o1);
+            cons_final_kernel<<<(a.count + 127) / 128, 128, 0, a.stream>>>(o1, a.inst, a.count,
+                                                                           a.rho0, o0);
+            break;
+        }
+        case AuxOp::CollideInPlace: {
+            if (a.compute == DT_F64) {
+                if constexpr (std::is_same<S, double>::value) {
+                    return a.collision == COLL_SRT
+                               ? collide_inplace_dispatch<Lat, S, double, COLL_SRT>(a, src, dst)
+                               : collide_inplace_dispatch<Lat, S, double, COLL_MINXENT4>(a, src, dst);
+                }
+                return cudaErrorInvalidValue;
+            }
+            return a.collision == COLL_SRT
+                       ? collide_inplace_dispatch<Lat, S, float, COLL_SRT>(a, src, dst)
+                       : collide_inplace_dispatch<Lat, S, float, COLL_MINXENT4>(a, src, dst);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <class Lat>
+cudaError_t aux_by_storage(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
+                           const double* p1, const double* p2, double* o0, double* o1, double* o2) {
+    switch (a.storage) {
+        case DT_F64: return aux_dispatch<Lat, double>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+        case DT_F32: return aux_dispatch<Lat, float>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+        case DT_F16: return aux_dispatch<Lat, __half>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+        case DT_BF16:
+            return aux_dispatch<Lat, __nv_bfloat16>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t run_aux(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
+                    const double* p1, const double* p2, double* o0, double* o1, double* o2) {
+    if (a.lattice == 2) return aux_by_storage<D2Q9>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+    return aux_by_storage<D1Q3>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+}
+
+}  // namespace lbm

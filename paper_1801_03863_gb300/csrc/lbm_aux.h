@@ -1,0 +1,47 @@
+// lbm_aux.h -- host-side entry points of the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// Blocks per instance of the first conservation pass (fixed, so the FP64
+// summation order never depends on the device).
+constexpr int CONS_PARTIALS = 64;
+
+enum class AuxOp { Init, SetF, CollideInPlace, Moments, GatherF, Conservation };
+
+struct AuxArgs {
+    int lattice;   // 1 = D1Q3, 2 = D2Q9
+    int storage;   // DT_*
+    int compute;   // DT_F64 or DT_F32
+    int collision; // COLL_*
+    int count;     // instances
+    int64_t max_nodes;
+    const InstDesc* inst;  // device
+    double rho0;
+    bool pulled;           // stored field is post-collision (pull to read f(t_n))
+    unsigned long long* status;
+    cudaStream_t stream;
+};
+
+// Init:           dst <- f^eq(rho=p0, ux=p1, uy=p2) deviations
+// SetF:           dst <- p0 (FP64 populations, [inst][a][y][x])
+// CollideInPlace: dst <- collide(src) without streaming
+// Moments:        o0, o1, o2 <- rho, ux, uy of f(t_n) read from src
+// GatherF:        o0 <- FP64 populations of f(t_n)
+// Conservation:   o0 <- per-instance totals (3 doubles each), o1 = partials scratch
+//                 (count * CONS_PARTIALS * 3 doubles)
+cudaError_t run_aux(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
+                    const double* p1, const double* p2, double* o0, double* o1, double* o2);
+
+// Fused step kernels, one translation unit per storage type.  Each returns
+// the __global__ function for (lattice, collision, V), or nullptr.
+const void* step_kernel_f64(int lattice, int collision, int V);
+const void* step_kernel_f32(int lattice, int collision, int V);
+const void* step_kernel_f16(int lattice, int collision, int V);
+const void* step_kernel_bf16(int lattice, int collision, int V);
+
+}  // namespace lbm

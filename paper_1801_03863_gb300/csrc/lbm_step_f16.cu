@@ -1,0 +1,25 @@
+// lbm_step_f16.cu -- fused step kernels with __half storage and float arithmetic.
+#include "lbm_aux.h"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+const void* step_kernel_f16(int lattice, int collision, int V) {
+    if (V == 4) {
+        if (lattice == 2)
+            return collision == COLL_SRT
+                       ? (const void*)&step_kernel<D2Q9, __half, float, 4, COLL_SRT>
+                       : (const void*)&step_kernel<D2Q9, __half, float, 4, COLL_MINXENT4>;
+        return (const void*)&step_kernel<D1Q3, __half, float, 4, COLL_MINXENT4>;
+    }
+    if (V == 8) {
+        if (lattice == 2)
+            return collision == COLL_SRT
+                       ? (const void*)&step_kernel<D2Q9, __half, float, 8, COLL_SRT>
+                       : (const void*)&step_kernel<D2Q9, __half, float, 8, COLL_MINXENT4>;
+        return (const void*)&step_kernel<D1Q3, __half, float, 8, COLL_MINXENT4>;
+    }
+    return nullptr;
+}
+
+}  // namespace lbm
