@@ -151,6 +151,22 @@ int lbm_conservation(lbm_ctx* ctx, double* out);
  * the stream, no sync (for checkpoints inside a timed step loop). */
 int lbm_conservation_device(lbm_ctx* ctx, double* out);
 
+/* lbm_conservation_device for callers that cannot allocate device memory
+ * (an application that owns every allocation through its own pool, a
+ * real-time loop that must not hit the allocator's synchronisation, a plugin
+ * whose host forbids new allocations).  The paper has no counterpart; this is
+ * an interface convenience.  The call allocates nothing: the reduction's
+ * scratch is a fixed array inside the library (6 MiB per device, kept until
+ * the process exits), enough for contexts of up to 4096 instances; larger
+ * contexts get LBM_ERR_ARG.  out: DEVICE pointer to 3*count doubles, same
+ * values as lbm_conservation_device.  The first call on a device looks up the
+ * array's device address; make that first call outside any CUDA stream
+ * capture.  All calls in the process share the array, so calls whose work
+ * overlaps on the GPU (different streams, different contexts) race: order
+ * them on one stream or synchronise between them.  Ordered on the context's
+ * stream; no sync. */
+int lbm_conservation_noalloc(lbm_ctx* ctx, double* out);
+
 /* Status counters summed over all instances since lbm_init:
  * counters[0] = nodes whose Newton step was skipped because some start
  * probability was <= 0 (the log of Eq. discrete_KLD is undefined there; the

@@ -352,6 +352,21 @@ int validate_dims(int lat, int32_t count, const int64_t* dims,
 
 }  // namespace
 
+namespace lbm {
+// Inputs of the conservation reduction of a context, for entry points that
+// live in other translation units.  Returns LBM_OK, or the code the public
+// conservation call would return for this context.
+int ctx_conservation_inputs(const lbm_ctx* ctx, AuxArgs* args, const void** src, int* count) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    *args = aux_args(ctx);
+    *src = ctx->buf[ctx->cur];
+    *count = ctx->count;
+    return LBM_OK;
+}
+}  // namespace lbm
+
 extern "C" {
 
 void lbm_default_opts(lbm_opts* o) {

@@ -32,7 +32,8 @@ BCS = {"periodic": LBM_BC_PERIODIC, "zero_gradient": LBM_BC_ZERO_GRADIENT, "cavi
 EXPORTS = (
     "lbm_default_opts", "lbm_required_bytes", "lbm_create", "lbm_create_batch", "lbm_init",
     "lbm_init_device", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_get_populations",
-    "lbm_set_populations", "lbm_conservation", "lbm_conservation_device", "lbm_status",
+    "lbm_set_populations", "lbm_conservation", "lbm_conservation_device",
+    "lbm_conservation_noalloc", "lbm_status",
     "lbm_status_instance",
     "lbm_launch_shape", "lbm_destroy", "lbm_status_string",
 )
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_set_populations": (ctypes.c_int, [P, P]),
             "lbm_conservation": (ctypes.c_int, [P, P]),
             "lbm_conservation_device": (ctypes.c_int, [P, P]),
+            "lbm_conservation_noalloc": (ctypes.c_int, [P, P]),
             "lbm_status": (ctypes.c_int, [P, P]),
             "lbm_status_instance": (ctypes.c_int, [P, I32, P]),
             "lbm_launch_shape": (ctypes.c_int, [P, P]),
@@ -202,6 +204,12 @@ def lbm_conservation(h, count: int) -> np.ndarray:
 
 def lbm_conservation_device(h, out_ptr) -> None:
     _check(load().lbm_conservation_device(h, out_ptr), "lbm_conservation_device")
+
+
+def lbm_conservation_noalloc(h, out_ptr) -> None:
+    """Conservation totals into device memory without any device allocation
+    (scratch in a fixed array inside the library; up to 4096 instances)."""
+    _check(load().lbm_conservation_noalloc(h, out_ptr), "lbm_conservation_noalloc")
 
 
 def lbm_status(h) -> dict:
