@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--compute", choices=["f32", "f64"], default="f32")
     p.add_argument("--storage", choices=["f16", "bf16", "f32", "f64"], default=None,
                    help="default: the workload's own storage type")
+    p.add_argument("--collision", choices=["minxent4", "srt"], default="minxent4",
+                   help="srt: the SRT-BGK twin kernel (bandwidth reference)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP64 comparison, e2e and CPU-baseline legs")
     return p.parse_args()
@@ -159,10 +161,10 @@ class Workload:
         self.nodes = int(sum(a * b for a, b in self.dims))
         self.q = 9 if self.lattice == "d2q9" else 3
 
-    def lattice_obj(self, compute: str, storage: str):
+    def lattice_obj(self, compute: str, storage: str, collision: str = "minxent4"):
         from paper_1801_03863_gb300 import lbm
         return lbm.Lattice(self.lattice, self.dims, self.nu, self.bc, u_lid=self.u_lid,
-                           compute=compute, storage=storage)
+                           compute=compute, storage=storage, collision=collision)
 
     def fields(self):
         return (self.rho, self.ux, self.uy) if self.q == 9 else (self.rho, self.ux)
@@ -356,14 +358,14 @@ def run_reference(args, dist):
 
 def config_for(args, wk, lat):
     c = {
-        "workload": WORKLOADS[wk.name] + f"; MinxEnt4, {args.compute.upper()} collide, "
+        "workload": WORKLOADS[wk.name] + f"; {args.collision.upper()}, {args.compute.upper()} collide, "
                     f"{args.storage.upper()} deviation storage, CUDA-graph step loop",
         "instances_per_gpu": len(wk.dims),
         "nodes_per_gpu": wk.nodes,
         "lattice": wk.lattice,
         "compute": args.compute,
         "storage": args.storage,
-        "collision": "minxent4",
+        "collision": args.collision,
         "conservation_every": CONS_EVERY,
         "l2": ("inputs larger than L2 (two population copies, no flush needed)"
                if 2 * wk.nodes * wk.bytes_per_lu(args.storage) // 2 > 129e6 else
@@ -385,7 +387,7 @@ def run_ours(args, dist):
 
     torch.cuda.set_device(dist.local)
     wk = Workload(args.workload, dist.rank, dist.world)
-    lat = wk.lattice_obj(args.compute, args.storage)
+    lat = wk.lattice_obj(args.compute, args.storage, args.collision)
     stream = lat.stream
     cons = torch.empty(3 * len(wk.dims), dtype=torch.float64, device="cuda")
 
@@ -437,8 +439,9 @@ def run_ours(args, dist):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tpn is None else tpn * wk.nodes,
                 "algorithmic_bytes_per_launch": wk.nodes * bpl,
-                "kernel": f"lbm::step_kernel<{wk.lattice.upper()}, {args.storage}, "
-                          f"{args.compute}, V={shape['V']}, MINXENT4>",
+                "kernel": f"lbm step kernel ({shape['kind']}) {wk.lattice.upper()} "
+                          f"{args.storage} storage, {args.compute} compute, "
+                          f"{args.collision.upper()}",
                 "avg_launch_ms": launch_ms}
 
     line = {

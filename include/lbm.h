@@ -45,6 +45,9 @@ typedef struct lbm_ctx lbm_ctx;
                                  sticky, reported by lbm_moments / lbm_status */
 #define LBM_ERR_STATE (-5)    /* call out of order (e.g. step before init)     */
 #define LBM_ERR_NODEV (-6)    /* no CUDA device, or not an sm_103 device       */
+#define LBM_ERR_TIMEOUT (-7)  /* a bounded device-side wait on an asynchronous
+                                 copy ran out; the step's outputs are invalid
+                                 (sticky, reported by lbm_status / lbm_moments) */
 
 /* Lattices: D2Q9 of Table I; D1Q3, its one-dimensional restriction
  * (velocities 0, +1, -1; weights 2/3, 1/6, 1/6). */
@@ -177,7 +180,10 @@ int lbm_status(lbm_ctx* ctx, int64_t* counters);
 int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
 
 /* Launch shape in use: out[0] = nodes per thread, out[1] = tile width in
- * thread chunks, out[2] = tile height in rows, out[3] = grid size (CTAs). */
+ * thread chunks, out[2] = tile height in rows, out[3] = grid size (CTAs),
+ * out[4] = kernel kind (0: register-chunk kernel; 1: shared-memory staged
+ * D2Q9 kernel, node pairs per thread, tile width 64/128/256 nodes chosen per
+ * instance -- out[1] and out[2] are 0 then). */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* out);
 
 /* Destroy a context (NULL-safe).  Frees library-owned memory only. */

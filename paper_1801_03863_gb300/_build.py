@@ -49,7 +49,17 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every CUDA source for sm_103a and link liblbm.so."""
+    """Compile every CUDA source for sm_103a and link liblbm.so.
+
+    LBM_NVCC_FLAGS (environment) adds compiler flags, e.g. -D overrides of the
+    kernels' tuning constants; a library built with it is rebuilt without it
+    on the next plain build."""
+    env_flags = tuple(os.environ.get("LBM_NVCC_FLAGS", "").split())
+    extra_flags = tuple(extra_flags) + env_flags
+    stamp = LIB + ".flags"
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if " ".join(extra_flags) != old:
+        force = True
     if not force and up_to_date():
         return LIB
     os.makedirs(OBJ, exist_ok=True)
@@ -73,6 +83,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(" ".join(extra_flags))
     return LIB
 
 

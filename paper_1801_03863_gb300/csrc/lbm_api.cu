@@ -1,6 +1,7 @@
 // lbm_api.cu -- the C ABI of liblbm (declared in include/lbm.h): context
 // lifetime, device memory layout, tile tables, the launch-shape autotuner,
 // CUDA-graph replay of the step loop, and host I/O.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,8 +26,12 @@ constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even)
 
 size_t dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
 
+// Launch shape.  kind 0: register-chunk kernel (V nodes per thread, tiles of
+// tw x th chunks); kind 1: shared-memory staged D2Q9 kernel (node pairs,
+// tiles of smem_tile_nodes() nodes, width per instance).
 struct Shape {
     int V, tw, th;
+    int kind = 0;
 };
 
 // Launch-shape candidates.  V (nodes per thread) is limited to the compiled
@@ -37,6 +42,7 @@ std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, in
     else if (storage == DT_F32) vs = {2, 4};
     else vs = {4, 8};
     std::vector<Shape> out;
+    if (lattice == 2 && storage != DT_F64) out.push_back({2, 0, 0, 1});
     for (int V : vs) {
         for (int block : {128, 256}) {
             for (int tw = 4; tw <= block; tw *= 2) {
@@ -58,8 +64,16 @@ Shape default_shape(int lattice, int storage) {
     return {8, 8, 16};
 }
 
-int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const Shape& s) {
+int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const Shape& s,
+                    int storage) {
     int64_t n = 0;
+    if (s.kind == 1) {
+        for (auto& d : dims) {
+            const int64_t X = smem_tile_width(d.first), R = smem_tile_nodes(storage) / X;
+            n += ((d.first + X - 1) / X) * ((d.second + R - 1) / R);
+        }
+        return n;
+    }
     for (auto& d : dims) {
         const int64_t chunks = (d.first + s.V - 1) / s.V;
         n += ((chunks + s.tw - 1) / s.tw) * ((d.second + s.th - 1) / s.th);
@@ -97,14 +111,21 @@ Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t
     }
     L.elems = off;
     L.total_nodes = node0;
-    for (const Shape& s : candidate_shapes(lattice, storage, L.max_nx, L.max_ny))
-        L.max_tiles = std::max(L.max_tiles, count_tiles(dims, s));
-    L.max_tiles = std::max(L.max_tiles, count_tiles(dims, default_shape(lattice, storage)));
+    // Tile-table capacity: a bound that holds for every register-chunk shape
+    // (V >= 2, tw >= 4, tw * th >= 128 threads) and the shared-memory kernel's
+    // tiling, so any shape the autotuner or LBM_SHAPE selects fits.
+    int64_t bound = 0;
+    for (auto& d : dims) {
+        const int64_t chunks = (d.first + 1) / 2;
+        bound += chunks * d.second / 128 + chunks / 4 + d.second + 1;
+    }
+    L.max_tiles = std::max(bound, count_tiles(dims, Shape{2, 0, 0, 1}, storage));
     return L;
 }
 
 struct Carve {
-    size_t buf_bytes, inst_off, tiles_off, status_off, partials_off, stage_off, total;
+    size_t buf_bytes, inst_off, tiles_off, status_off, partials_off, stage_off, tmap_off, err_off,
+        total;
 };
 
 Carve carve(const Layout& L, int lattice, int storage, int count) {
@@ -123,6 +144,10 @@ Carve carve(const Layout& L, int lattice, int storage, int count) {
     p += al(sizeof(double) * 3 * (size_t)CONS_PARTIALS * count);
     c.stage_off = p;
     p += al(sizeof(double) * std::max<int64_t>(3 * L.total_nodes, Q * L.total_nodes));
+    c.tmap_off = p;  // two TMA tensor maps (one per population buffer) per instance
+    p += al(2 * sizeof(CUtensorMapOpaque) * count);
+    c.err_off = p;
+    p += 256;
     c.total = p;
     return c;
 }
@@ -147,6 +172,9 @@ struct lbm_ctx {
     unsigned long long* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_stage = nullptr;
+    CUtensorMapOpaque* d_tmaps = nullptr;  // [buffer][instance]
+    unsigned int* d_error = nullptr;
+    bool tmaps_ready = false;
     std::vector<TileDesc> tiles;
     bool initialized = false;
     bool post = false;  // stored field is post-collision
@@ -154,6 +182,7 @@ struct lbm_ctx {
     Shape shape{};
     const void* kern = nullptr;
     int grid = 0;
+    size_t smem = 0;  // dynamic shared memory of the step kernel
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool failed = false;
 };
@@ -200,6 +229,16 @@ AuxArgs aux_args(const lbm_ctx* ctx) {
 
 std::vector<TileDesc> build_tiles(const lbm_ctx* ctx, const Shape& s) {
     std::vector<TileDesc> t;
+    if (s.kind == 1) {
+        for (int i = 0; i < ctx->count; ++i) {
+            const InstDesc& in = ctx->layout.inst[i];
+            const int X = smem_tile_width(in.nx), R = smem_tile_nodes(ctx->storage) / X;
+            for (int64_t y0 = 0; y0 < in.ny; y0 += R)
+                for (int64_t x0 = 0; x0 < in.nx; x0 += X)
+                    t.push_back({(int32_t)i, (int32_t)x0, (int32_t)y0, (int32_t)X});
+        }
+        return t;
+    }
     for (int i = 0; i < ctx->count; ++i) {
         const InstDesc& in = ctx->layout.inst[i];
         const int64_t chunks = (in.nx + s.V - 1) / s.V;
@@ -216,9 +255,24 @@ int ilog2(int v) {
     return r;
 }
 
+int build_tensor_maps(lbm_ctx* ctx);
+
 // Make shape s current: tile table to the device, kernel and grid size.
 int apply_shape(lbm_ctx* ctx, const Shape& s) {
-    const void* k = find_step_kernel(ctx->lattice, ctx->storage, ctx->collision, s.V);
+    const void* k = nullptr;
+    size_t smem = 0;
+    if (s.kind == 1) {
+        if (ctx->lattice != 2 || ctx->compute != DT_F32) return LBM_ERR_ARG;
+        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, &smem);
+        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, &smem);
+        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, &smem);
+        if (!k) return LBM_ERR_ARG;
+        LBM_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int rc = build_tensor_maps(ctx);
+        if (rc != LBM_OK) return rc;
+    } else {
+        k = find_step_kernel(ctx->lattice, ctx->storage, ctx->collision, s.V);
+    }
     if (!k) return LBM_ERR_ARG;
     std::vector<TileDesc> t = build_tiles(ctx, s);
     if ((int64_t)t.size() > ctx->layout.max_tiles) return LBM_ERR_ARG;
@@ -236,19 +290,67 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     LBM_CK(cudaMemcpyAsync(ctx->d_inst, ctx->layout.inst.data(), sizeof(InstDesc) * ctx->count,
                            cudaMemcpyHostToDevice, ctx->stream));
     LBM_CK(cudaStreamSynchronize(ctx->stream));
-    const int block = s.tw * s.th;
+    const int block = s.kind == 1 ? 256 : s.tw * s.th;
     int per_sm = 0;
-    LBM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0));
+    LBM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     per_sm = std::max(per_sm, 1);
     const int64_t g = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, (int64_t)t.size());
     ctx->tiles.swap(t);
     ctx->shape = s;
     ctx->kern = k;
+    ctx->smem = smem;
     ctx->grid = (int)std::max<int64_t>(g, 1);
     for (int p = 0; p < 2; ++p) {
         if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
         ctx->graph[p] = nullptr;
     }
+    return LBM_OK;
+}
+
+// TMA tensor maps of both population buffers: per instance a 4-D view
+// (element within a 16-byte chunk, chunk, row, plane) with a box of one
+// tile of the staged kernel plus a one-chunk halo on each side in x.
+int build_tensor_maps(lbm_ctx* ctx) {
+    if (ctx->tmaps_ready) return LBM_OK;
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    LBM_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                            &q));
+    if (!fn || q != cudaDriverEntryPointSuccess) return LBM_ERR_CUDA;
+    EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
+    const size_t es = dtype_bytes(ctx->storage);
+    const int E = (int)(16 / es);
+    const int tile_nodes = smem_tile_nodes(ctx->storage);
+    std::vector<CUtensorMap> maps(2 * (size_t)ctx->count);
+    for (int b = 0; b < 2; ++b) {
+        for (int i = 0; i < ctx->count; ++i) {
+            const InstDesc& in = ctx->layout.inst[i];
+            const int X = smem_tile_width(in.nx), R = tile_nodes / X;
+            void* base = ctx->buf[b] + (size_t)in.off * es;
+            cuuint64_t dims[4] = {(cuuint64_t)E, (cuuint64_t)(in.pitch / E), (cuuint64_t)in.ny, 9};
+            cuuint64_t strides[3] = {16, (cuuint64_t)in.pitch * es, (cuuint64_t)in.plane * es};
+            cuuint32_t box[4] = {(cuuint32_t)E, (cuuint32_t)(X / E + 2), (cuuint32_t)R, 1};
+            cuuint32_t estr[4] = {1, 1, 1, 1};
+            CUresult r = encode(&maps[(size_t)b * ctx->count + i],
+                                es == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                if (getenv("LBM_DEBUG")) fprintf(stderr, "liblbm: tensor map encode failed (%d)\n", (int)r);
+                return LBM_ERR_CUDA;
+            }
+        }
+    }
+    static_assert(sizeof(CUtensorMap) == sizeof(CUtensorMapOpaque), "tensor map size");
+    LBM_CK(cudaMemcpyAsync(ctx->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tmaps_ready = true;
     return LBM_OK;
 }
 
@@ -260,18 +362,20 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
     a.tiles = ctx->d_tiles;
     a.ntiles = (int32_t)ctx->tiles.size();
     a.tw = ctx->shape.tw;
-    a.tw_log2 = ilog2(ctx->shape.tw);
+    a.tw_log2 = ctx->shape.tw > 0 ? ilog2(ctx->shape.tw) : 0;
     a.th = ctx->shape.th;
     a.rho0 = ctx->rho0;
     a.status = ctx->d_status;
+    a.tmaps = ctx->d_tmaps + (size_t)src * ctx->count;
+    a.error = ctx->d_error;
     return a;
 }
 
 cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
     StepArgs a = step_args(ctx, src);
     void* params[] = {&a};
-    return cudaLaunchKernel(ctx->kern, dim3(ctx->grid), dim3(ctx->shape.tw * ctx->shape.th),
-                            params, 0, s);
+    const int block = ctx->shape.kind == 1 ? 256 : ctx->shape.tw * ctx->shape.th;
+    return cudaLaunchKernel(ctx->kern, dim3(ctx->grid), dim3(block), params, ctx->smem, s);
 }
 
 // Time candidate shapes on the zeroed (rest-state) buffers and keep the fastest.
@@ -310,6 +414,10 @@ int autotune(lbm_ctx* ctx) {
 bool parse_shape_env(Shape* s) {
     const char* e = getenv("LBM_SHAPE");
     if (!e) return false;
+    if (strcmp(e, "smem") == 0) {
+        *s = {2, 0, 0, 1};
+        return true;
+    }
     int v, tw, th;
     if (sscanf(e, "%d,%d,%d", &v, &tw, &th) != 3) return false;
     *s = {v, tw, th};
@@ -470,6 +578,8 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
     ctx->d_status = reinterpret_cast<unsigned long long*>(ctx->mem + ctx->cv.status_off);
     ctx->d_partials = reinterpret_cast<double*>(ctx->mem + ctx->cv.partials_off);
     ctx->d_stage = reinterpret_cast<double*>(ctx->mem + ctx->cv.stage_off);
+    ctx->d_tmaps = reinterpret_cast<CUtensorMapOpaque*>(ctx->mem + ctx->cv.tmap_off);
+    ctx->d_error = reinterpret_cast<unsigned int*>(ctx->mem + ctx->cv.err_off);
     auto fail = [&](int code) {
         lbm_destroy(ctx);
         return code;
@@ -513,6 +623,7 @@ int lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, const dou
                    nullptr));
     LBM_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned long long) * 2 * ctx->count,
                            ctx->stream));
+    LBM_CK(cudaMemsetAsync(ctx->d_error, 0, sizeof(unsigned int), ctx->stream));
     ctx->post = false;
     ctx->initialized = true;
     ctx->steps = 0;
@@ -617,7 +728,10 @@ int lbm_status(lbm_ctx* ctx, int64_t* counters) {
         counters[1] += (int64_t)h[2 * i + 1];
     }
     counters[2] = ctx->steps;
-    return LBM_OK;
+    unsigned int err = 0;
+    LBM_CK(cudaMemcpyAsync(&err, ctx->d_error, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return err ? LBM_ERR_TIMEOUT : LBM_OK;
 }
 
 int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
@@ -697,6 +811,7 @@ int lbm_launch_shape(lbm_ctx* ctx, int32_t* out) {
     out[1] = ctx->shape.tw;
     out[2] = ctx->shape.th;
     out[3] = ctx->grid;
+    out[4] = ctx->shape.kind;
     return LBM_OK;
 }
 
@@ -709,6 +824,7 @@ const char* lbm_status_string(int code) {
         case LBM_ERR_UNSTABLE: return "unstable: negative or non-finite population";
         case LBM_ERR_STATE: return "call out of order (context not initialised)";
         case LBM_ERR_NODEV: return "no sm_103 CUDA device";
+        case LBM_ERR_TIMEOUT: return "a bounded device-side wait ran out (data copy never completed)";
     }
     return "unknown status code";
 }

@@ -25,67 +25,113 @@
 //     delta_a = 3 v.u + 9/2 (v.u)^2 - 3/2 u^2
 //             + (1 - omega)/(4 W_a) [(v_x^2 - v_y^2)_a s8 + (v_x v_y)_a s9],
 //     s8 = P_xx/rho - (u_x^2 - u_y^2),  s9 = P_xy/rho - u_x u_y,
-// so ln(p_a/W_a) = log1p(delta_a) is formed without cancellation.
+// so ln(p_a/W_a) = ln(1 + delta_a) is formed without cancellation.
+//
+// The rules are templates over the number type T of lbm_num.cuh (double,
+// float, or F2 = two nodes at once); a[b] below always means a * b + c with
+// one rounding (Num<T>::mad).
 #pragma once
 #include "lbm_common.cuh"
+#include "lbm_num.cuh"
 
 namespace lbm {
 
-// Math used by the collisions.  FP64: IEEE division and the library log1p.
-// FP32: the library log1pf and a correctly rounded reciprocal.
-template <typename T> struct Math;
-template <> struct Math<double> {
-    __device__ static __forceinline__ double log1p_(double x) { return log1p(x); }
-    __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
-};
-template <> struct Math<float> {
-    __device__ static __forceinline__ float log1p_(float x) { return log1pf(x); }
-    __device__ static __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-};
+// Status bits of lane l are (ST_* << 2 l).
+template <typename T>
+__device__ __forceinline__ uint32_t lane_status(typename Num<T>::Pred skipped_ok,
+                                                typename Num<T>::Pred finite_nonneg) {
+    if constexpr (Num<T>::LANES == 1) {
+        return (skipped_ok ? 0u : ST_NEWTON_SKIPPED) | (finite_nonneg ? 0u : ST_UNSTABLE);
+    } else {
+        return (skipped_ok.x ? 0u : ST_NEWTON_SKIPPED) | (finite_nonneg.x ? 0u : ST_UNSTABLE) |
+               ((skipped_ok.y ? 0u : ST_NEWTON_SKIPPED) << 2) |
+               ((finite_nonneg.y ? 0u : ST_UNSTABLE) << 2);
+    }
+}
 
-// 4x4 symmetric positive definite solve by LDL^T (no square roots).
-// A given as its 10 unique entries; returns x.
+// Stability criterion of Sec. IV.H on f^post_a = W_a rho0 + out_a: every
+// population finite and >= 0.  Returns a per-lane "all good" predicate.
+template <typename T, int Q>
+__device__ __forceinline__ typename Num<T>::Pred finite_nonneg(const T (&out)[Q],
+                                                               const double (&w)[Q], T rho0) {
+    using N = Num<T>;
+    typename N::Pred ok;
+    if constexpr (N::LANES == 1) {
+        ok = true;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) ok = ok && (out[a] >= -T(w[a]) * rho0);
+        // out >= c is false for NaN; a +inf population needs a non-finite input
+        // and then the mass sum is not finite
+        T s = out[0];
+#pragma unroll
+        for (int a = 1; a < Q; ++a) s = s + out[a];
+        ok = ok && (fabs(s) < T(1e30));
+    } else {
+        bool okx = true, oky = true;
+        float sx = 0.f, sy = 0.f;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float lo = -(float)w[a] * rho0.v.x;
+            okx = okx && (out[a].v.x >= lo);
+            oky = oky && (out[a].v.y >= lo);
+        }
+        T s = out[0];
+#pragma unroll
+        for (int a = 1; a < Q; ++a) s = s + out[a];
+        sx = s.v.x;
+        sy = s.v.y;
+        ok = {okx && (fabsf(sx) < 1e30f), oky && (fabsf(sy) < 1e30f)};
+    }
+    return ok;
+}
+
+// 4x4 symmetric positive definite solve A x = b by 2x2 blocks:
+//   A = [P B; B^T C],  P, C 2x2,
+//   Schur complement Z = C - B^T P^-1 B (SPD when A is),
+//   x2 = Z^-1 (b2 - B^T P^-1 b1),  x1 = P^-1 (b1 - B x2).
+// Two reciprocals (of det P and det Z) and a short dependency chain.
+// A given as its 10 unique entries, unknown order (1, 2 | 3, 4).
 template <typename T>
 __device__ __forceinline__ void spd4_solve(T a11, T a21, T a22, T a31, T a32, T a33, T a41, T a42,
                                            T a43, T a44, T b1, T b2, T b3, T b4, T& x1, T& x2,
                                            T& x3, T& x4) {
-    const T d1 = a11;
-    const T i1 = Math<T>::rcp(d1);
-    const T l21 = a21 * i1, l31 = a31 * i1, l41 = a41 * i1;
-    const T d2 = a22 - l21 * a21;
-    const T i2 = Math<T>::rcp(d2);
-    const T e32 = a32 - l31 * a21;  // (A32 - L31 D1 L21)
-    const T e42 = a42 - l41 * a21;
-    const T l32 = e32 * i2, l42 = e42 * i2;
-    const T d3 = a33 - l31 * a31 - l32 * e32;
-    const T i3 = Math<T>::rcp(d3);
-    const T e43 = a43 - l41 * a31 - l42 * e32;
-    const T l43 = e43 * i3;
-    const T d4 = a44 - l41 * a41 - l42 * e42 - l43 * e43;
-    const T i4 = Math<T>::rcp(d4);
-    // forward (unit lower), diagonal, backward
-    const T z1 = b1;
-    const T z2 = b2 - l21 * z1;
-    const T z3 = b3 - l31 * z1 - l32 * z2;
-    const T z4 = b4 - l41 * z1 - l42 * z2 - l43 * z3;
-    x4 = z4 * i4;
-    x3 = z3 * i3 - l43 * x4;
-    x2 = z2 * i2 - l32 * x3 - l42 * x4;
-    x1 = z1 * i1 - l21 * x2 - l31 * x3 - l41 * x4;
+    using N = Num<T>;
+    // P^-1 = [a22 -a21; -a21 a11] / det P
+    const T ip = N::rcp(N::mad(a11, a22, -(a21 * a21)));
+    const T p11 = a22 * ip, p12 = -(a21 * ip), p22 = a11 * ip;
+    // W = P^-1 B, B = [a31 a41; a32 a42]
+    const T w11 = N::mad(p11, a31, p12 * a32), w12 = N::mad(p11, a41, p12 * a42);
+    const T w21 = N::mad(p12, a31, p22 * a32), w22 = N::mad(p12, a41, p22 * a42);
+    // Z = C - B^T W
+    const T z11 = a33 - N::mad(a31, w11, a32 * w21);
+    const T z12 = a43 - N::mad(a31, w12, a32 * w22);
+    const T z22 = a44 - N::mad(a41, w12, a42 * w22);
+    const T iz = N::rcp(N::mad(z11, z22, -(z12 * z12)));
+    // y1 = P^-1 b1 ; r2 = b2 - B^T y1
+    const T y1 = N::mad(p11, b1, p12 * b2), y2 = N::mad(p12, b1, p22 * b2);
+    const T r3 = b3 - N::mad(a31, y1, a32 * y2);
+    const T r4 = b4 - N::mad(a41, y1, a42 * y2);
+    // x2 = Z^-1 r2 ; x1 = y1 - W x2
+    x3 = N::mad(z22, r3, -(z12 * r4)) * iz;
+    x4 = N::mad(z11, r4, -(z12 * r3)) * iz;
+    x1 = y1 - N::mad(w11, x3, w12 * x4);
+    x2 = y2 - N::mad(w21, x3, w22 * x4);
 }
 
 // ---------------------------------------------------------------------------
-// D2Q9 MinxEnt4 collision of one fluid node.
+// D2Q9 MinxEnt4 collision of one fluid node (or two, T = F2).
 //   d      pulled pre-collision deviations f_a - W_a rho0
 //   rho0   reference density; omega = 1/tau
 //   out    post-collision deviations
-// Returns ST_* bits: ST_NEWTON_SKIPPED when some p^start_a <= 0 (the node
-// keeps p^start, which meets every constraint), ST_UNSTABLE when some
-// post-collision population is negative or not finite.
+// Returns ST_* bits per lane: ST_NEWTON_SKIPPED when some p^start_a <= 0
+// (the node keeps p^start, which meets every constraint), ST_UNSTABLE when
+// some post-collision population is negative or not finite.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T omega, T (&out)[9]) {
-    const T W0 = T(4.0 / 9.0), WA = T(1.0 / 9.0), WD = T(1.0 / 36.0);
+    using N = Num<T>;
+    constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
     // Moments of the pulled state (Sec. II.A) and the stress moments
     // M8 = sum f (v_x^2 - v_y^2), M9 = sum f v_x v_y (rows 8, 9 of T).
     const T drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
@@ -95,114 +141,105 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
     const T pxx = (d[1] + d[3]) - (d[2] + d[4]);
     const T pxy = (d[5] + d[7]) - (d[6] + d[8]);
     const T rho = rho0 + drho;
-    const T ir = Math<T>::rcp(rho);
+    const T ir = N::rcp(rho);
     const T ux = jx * ir, uy = jy * ir;
     const T uxx = ux * ux, uyy = uy * uy;
     // Non-equilibrium stress relaxed at 1/tau (Eqs. discreteviscoconst/isoconst):
-    // c8 - M8eq = (1 - omega)(M8pre - M8eq), and likewise for M9.
-    const T k = (T(1) - omega) * T(0.25);
-    const T a8 = k * (pxx * ir - (uxx - uyy));
-    const T a9 = k * (pxy * ir - ux * uy);
-    // delta_a = p^start_a / W_a - 1.
+    // c8 - M8eq = (1 - omega)(M8pre - M8eq), likewise for M9; scaled by 1/(4 W).
+    const T k = (T(1.0) - omega) * T(0.25);
+    const T c8 = (T(9.0) * k) * N::mad(pxx, ir, uyy - uxx);
+    const T c9 = (T(36.0) * k) * N::mad(pxy, ir, -(ux * uy));
+    // delta_a = p^start_a / W_a - 1
     const T b0 = T(-1.5) * (uxx + uyy);
-    const T sx = T(4.5) * uxx + b0 + T(9) * a8;
-    const T sy = T(4.5) * uyy + b0 - T(9) * a8;
+    const T sx = N::mad(T(4.5), uxx, b0 + c8);
+    const T sy = N::mad(T(4.5), uyy, b0 - c8);
     const T sp_ = ux + uy, dm_ = uy - ux;
-    const T sp = T(4.5) * sp_ * sp_ + b0 + T(36) * a9;
-    const T sm = T(4.5) * dm_ * dm_ + b0 - T(36) * a9;
+    const T sp = N::mad(T(4.5) * sp_, sp_, b0 + c9);
+    const T sm = N::mad(T(4.5) * dm_, dm_, b0 - c9);
     T del[9];
     del[0] = b0;
-    del[1] = sx + T(3) * ux;
-    del[3] = sx - T(3) * ux;
-    del[2] = sy + T(3) * uy;
-    del[4] = sy - T(3) * uy;
-    del[5] = sp + T(3) * sp_;
-    del[7] = sp - T(3) * sp_;
-    del[6] = sm + T(3) * dm_;
-    del[8] = sm - T(3) * dm_;
+    del[1] = N::mad(T(3.0), ux, sx);
+    del[3] = N::mad(T(-3.0), ux, sx);
+    del[2] = N::mad(T(3.0), uy, sy);
+    del[4] = N::mad(T(-3.0), uy, sy);
+    del[5] = N::mad(T(3.0), sp_, sp);
+    del[7] = N::mad(T(-3.0), sp_, sp);
+    del[6] = N::mad(T(3.0), dm_, sm);
+    del[8] = N::mad(T(-3.0), dm_, sm);
 
-    T mn = del[0];
+    // y_a = p^start_a / W_a; all positive <=> the logarithms exist (reading C-NEG)
+    T y[9];
 #pragma unroll
-    for (int a = 1; a < 9; ++a) mn = fmin(mn, del[a]);
+    for (int a = 0; a < 9; ++a) y[a] = T(1.0) + del[a];
+    T mn = N::vmin(N::vmin(N::vmin(y[0], y[1]), N::vmin(y[2], y[3])),
+                   N::vmin(N::vmin(y[4], y[5]), N::vmin(N::vmin(y[6], y[7]), y[8])));
+    const typename N::Pred ok = N::gt(mn, T(0.0));
 
-    uint32_t st = 0;
-    T t[9];
-    if (mn > T(-1)) {
-        // ln(p/W) and 1/p (scaled by W: q_a = 1/(1 + delta_a) = W_a / p_a).
-        T L[9], q[9];
+    // ln(p/W) (natural or base-2 logs, see Num::LOG_SCALE) and q_a = W_a / p_a
+    T L[9], q[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            L[a] = Math<T>::log1p_(del[a]);
-            q[a] = Math<T>::rcp(T(1) + del[a]);
-        }
-        // 1/p_a = q_a / W_a: rest 9/4 q, axis 9 q, diagonal 36 q.  A is formed
-        // divided by 9 (coefficients 1/4, 1, 4); the solution is rescaled below.
-        const T Q0 = T(0.25) * q[0];
-        const T Qa = (q[1] + q[2]) + (q[3] + q[4]);
-        const T Qd = T(4) * ((q[5] + q[6]) + (q[7] + q[8]));
-        const T d13 = q[1] - q[3], d24 = q[2] - q[4];
-        const T t57 = T(4) * (q[5] - q[7]), t68 = T(4) * (q[6] - q[8]);
-        const T Dx = t57 - t68;  // 4(q5 - q6 - q7 + q8)
-        const T Dy = t57 + t68;  // 4(q5 + q6 - q7 - q8)
-        const T Dxy = T(4) * ((q[5] + q[7]) - (q[6] + q[8]));
-        // rows of T used: e (M2), eps (M3), q_x (M5), q_y (M7)
-        const T A_ee = T(16) * Q0 + Qa + T(4) * Qd;
-        const T A_ep = T(-16) * Q0 + T(2) * Qa + T(2) * Qd;
-        const T A_pp = T(16) * Q0 + T(4) * Qa + Qd;
-        const T A_ex = T(2) * d13 + T(2) * Dx;
-        const T A_px = T(4) * d13 + Dx;
-        const T A_xx = T(4) * (q[1] + q[3]) + Qd;
-        const T A_ey = T(2) * d24 + T(2) * Dy;
-        const T A_py = T(4) * d24 + Dy;
-        const T A_yy = T(4) * (q[2] + q[4]) + Qd;
-        const T A_xy = Dxy;
-        const T La = (L[1] + L[2]) + (L[3] + L[4]);
-        const T Ld = (L[5] + L[6]) + (L[7] + L[8]);
-        const T l57 = L[5] - L[7], l68 = L[6] - L[8];
-        const T b_e = T(-4) * L[0] - La + T(2) * Ld;
-        const T b_p = T(4) * L[0] - T(2) * La + Ld;
-        const T b_x = T(2) * (L[3] - L[1]) + (l57 - l68);
-        const T b_y = T(2) * (L[4] - L[2]) + (l57 + l68);
-        T se, sps, sx_, sy_;
-        spd4_solve<T>(A_ee, A_ep, A_pp, A_ex, A_px, A_xx, A_ey, A_py, A_xy, A_yy, b_e, b_p, b_x,
-                      b_y, se, sps, sx_, sy_);
-        // (T^T s~)_a; the 1/9 from A's scaling goes into rho below.
-        const T ce = -se - T(2) * sps;
-        const T cd = T(2) * se + sps;
-        const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
-        t[0] = T(4) * (sps - se);
-        t[1] = ce - T(2) * sx_;
-        t[3] = ce + T(2) * sx_;
-        t[2] = ce - T(2) * sy_;
-        t[4] = ce + T(2) * sy_;
-        t[5] = cd + pxy_;
-        t[7] = cd - pxy_;
-        t[6] = cd - mxy_;
-        t[8] = cd + mxy_;
-    } else {
-        st |= ST_NEWTON_SKIPPED;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) t[a] = T(0);
+    for (int a = 0; a < 9; ++a) {
+        L[a] = N::lnp(del[a], y[a]);
+        q[a] = N::rcp(y[a]);
     }
-    // d^post_a = W_a (drho + rho delta_a) - rho (T^T s~)_a
-    const T rs = rho * T(1.0 / 9.0);
-    const T w0r = W0 * rho, war = WA * rho, wdr = WD * rho;
-    out[0] = W0 * drho + w0r * del[0] - rs * t[0];
+    // A/9 with 1/p_a = q_a / W_a: rest 9/4 q, axis 9 q, diagonal 36 q.
+    const T p13 = q[1] + q[3], p24 = q[2] + q[4];
+    const T d13 = q[1] - q[3], d24 = q[2] - q[4];
+    const T s57 = q[5] + q[7], s68 = q[6] + q[8];
+    const T d57 = q[5] - q[7], d68 = q[6] - q[8];
+    const T Qa = p13 + p24;
+    const T qd = s57 + s68;
+    const T dx = d57 - d68, dy = d57 + d68;
+    // rows of T used: e (M2), eps (M3), q_x (M5), q_y (M7)
+    const T A_ee = N::mad(T(16.0), qd, N::mad(T(4.0), q[0], Qa));
+    const T A_ep = N::mad(T(8.0), qd, N::mad(T(-4.0), q[0], Qa + Qa));
+    const T A_pp = T(4.0) * (q[0] + Qa + qd);
+    const T A_ex = N::mad(T(8.0), dx, d13 + d13);
+    const T A_px = T(4.0) * (d13 + dx);
+    const T A_xx = T(4.0) * (p13 + qd);
+    const T A_ey = N::mad(T(8.0), dy, d24 + d24);
+    const T A_py = T(4.0) * (d24 + dy);
+    const T A_yy = T(4.0) * (p24 + qd);
+    const T A_xy = T(4.0) * (s57 - s68);
+    const T La = (L[1] + L[2]) + (L[3] + L[4]);
+    const T Ld = (L[5] + L[6]) + (L[7] + L[8]);
+    const T l57 = L[5] - L[7], l68 = L[6] - L[8];
+    const T b_e = N::mad(T(-4.0), L[0], N::mad(T(2.0), Ld, -La));
+    const T b_p = N::mad(T(4.0), L[0], N::mad(T(-2.0), La, Ld));
+    const T b_x = N::mad(T(2.0), L[3] - L[1], l57 - l68);
+    const T b_y = N::mad(T(2.0), L[4] - L[2], l57 + l68);
+    T se, sps, sx_, sy_;
+    spd4_solve<T>(A_ee, A_ep, A_pp, A_ex, A_px, A_xx, A_ey, A_py, A_xy, A_yy, b_e, b_p, b_x, b_y,
+                  se, sps, sx_, sy_);
+    // a node whose start point is not positive keeps p^start (reading C-NEG)
+    se = N::sel(ok, se, T(0.0));
+    sps = N::sel(ok, sps, T(0.0));
+    sx_ = N::sel(ok, sx_, T(0.0));
+    sy_ = N::sel(ok, sy_, T(0.0));
+    // (T^T s~)_a
+    T t[9];
+    const T ce = N::mad(T(-2.0), sps, -se);
+    const T cd = N::mad(T(2.0), se, sps);
+    const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
+    t[0] = T(4.0) * (sps - se);
+    t[1] = N::mad(T(-2.0), sx_, ce);
+    t[3] = N::mad(T(2.0), sx_, ce);
+    t[2] = N::mad(T(-2.0), sy_, ce);
+    t[4] = N::mad(T(2.0), sy_, ce);
+    t[5] = cd + pxy_;
+    t[7] = cd - pxy_;
+    t[6] = cd - mxy_;
+    t[8] = cd + mxy_;
+    // d^post_a = W_a (drho + rho delta_a) - rho (T^T s~)_a; the 1/9 of A's
+    // scaling and the log base go into the last factor.
+    const T rs = rho * T(N::LOG_SCALE / 9.0);
 #pragma unroll
-    for (int a = 1; a < 5; ++a) out[a] = WA * drho + war * del[a] - rs * t[a];
-#pragma unroll
-    for (int a = 5; a < 9; ++a) out[a] = WD * drho + wdr * del[a] - rs * t[a];
-    // Stability criterion of Sec. IV.H: f^post = W rho0 + d^post finite, >= 0.
-    T fmn = (out[0] + W0 * rho0) * T(9.0 / 4.0);
-#pragma unroll
-    for (int a = 1; a < 5; ++a) fmn = fmin(fmn, (out[a] + WA * rho0) * T(9));
-#pragma unroll
-    for (int a = 5; a < 9; ++a) fmn = fmin(fmn, (out[a] + WD * rho0) * T(36));
-    T fsum = out[0];
-#pragma unroll
-    for (int a = 1; a < 9; ++a) fsum += out[a];
-    if (!(fmn >= T(0)) || !isfinite(fsum)) st |= ST_UNSTABLE;
-    return st;
+    for (int a = 0; a < 9; ++a) {
+        const T wa = T(W[a]);
+        out[a] = N::mad(-rs, t[a], N::mad(wa * rho, del[a], wa * drho));
+    }
+    typename N::Pred notskip = ok;
+    return lane_status<T>(notskip, finite_nonneg<T, 9>(out, W, rho0));
 }
 
 // ---------------------------------------------------------------------------
@@ -210,51 +247,41 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ uint32_t srt_d2q9(const T (&d)[9], T rho0, T omega, T (&out)[9]) {
-    const T W0 = T(4.0 / 9.0), WA = T(1.0 / 9.0), WD = T(1.0 / 36.0);
+    using N = Num<T>;
+    constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
     const T drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     const T a57 = d[5] - d[7], a86 = d[8] - d[6];
     const T jx = (d[1] - d[3]) + a57 + a86;
     const T jy = (d[2] - d[4]) + a57 - a86;
     const T rho = rho0 + drho;
-    const T ir = Math<T>::rcp(rho);
+    const T ir = N::rcp(rho);
     const T ux = jx * ir, uy = jy * ir;
-    const T b0 = T(-1.5) * (ux * ux + uy * uy);
-    const T sx = T(4.5) * ux * ux + b0, sy = T(4.5) * uy * uy + b0;
+    const T uxx = ux * ux, uyy = uy * uy;
+    const T b0 = T(-1.5) * (uxx + uyy);
+    const T sx = N::mad(T(4.5), uxx, b0), sy = N::mad(T(4.5), uyy, b0);
     const T sp_ = ux + uy, dm_ = uy - ux;
-    const T sp = T(4.5) * sp_ * sp_ + b0, sm = T(4.5) * dm_ * dm_ + b0;
+    const T sp = N::mad(T(4.5) * sp_, sp_, b0), sm = N::mad(T(4.5) * dm_, dm_, b0);
     T xi[9];
     xi[0] = b0;
-    xi[1] = sx + T(3) * ux;
-    xi[3] = sx - T(3) * ux;
-    xi[2] = sy + T(3) * uy;
-    xi[4] = sy - T(3) * uy;
-    xi[5] = sp + T(3) * sp_;
-    xi[7] = sp - T(3) * sp_;
-    xi[6] = sm + T(3) * dm_;
-    xi[8] = sm - T(3) * dm_;
-    const T w0r = W0 * rho, war = WA * rho, wdr = WD * rho;
-    T deq;
-    deq = W0 * drho + w0r * xi[0];
-    out[0] = d[0] + omega * (deq - d[0]);
+    xi[1] = N::mad(T(3.0), ux, sx);
+    xi[3] = N::mad(T(-3.0), ux, sx);
+    xi[2] = N::mad(T(3.0), uy, sy);
+    xi[4] = N::mad(T(-3.0), uy, sy);
+    xi[5] = N::mad(T(3.0), sp_, sp);
+    xi[7] = N::mad(T(-3.0), sp_, sp);
+    xi[6] = N::mad(T(3.0), dm_, sm);
+    xi[8] = N::mad(T(-3.0), dm_, sm);
 #pragma unroll
-    for (int a = 1; a < 5; ++a) {
-        deq = WA * drho + war * xi[a];
-        out[a] = d[a] + omega * (deq - d[a]);
+    for (int a = 0; a < 9; ++a) {
+        const T wa = T(W[a]);
+        const T deq = N::mad(wa * rho, xi[a], wa * drho);
+        out[a] = N::mad(omega, deq - d[a], d[a]);
     }
-#pragma unroll
-    for (int a = 5; a < 9; ++a) {
-        deq = WD * drho + wdr * xi[a];
-        out[a] = d[a] + omega * (deq - d[a]);
-    }
-    T fmn = (out[0] + W0 * rho0) * T(9.0 / 4.0);
-#pragma unroll
-    for (int a = 1; a < 5; ++a) fmn = fmin(fmn, (out[a] + WA * rho0) * T(9));
-#pragma unroll
-    for (int a = 5; a < 9; ++a) fmn = fmin(fmn, (out[a] + WD * rho0) * T(36));
-    T fsum = out[0];
-#pragma unroll
-    for (int a = 1; a < 9; ++a) fsum += out[a];
-    return (!(fmn >= T(0)) || !isfinite(fsum)) ? ST_UNSTABLE : 0u;
+    typename N::Pred all;
+    if constexpr (N::LANES == 1) all = true;
+    else all = {true, true};
+    return lane_status<T>(all, finite_nonneg<T, 9>(out, W, rho0));
 }
 
 // ---------------------------------------------------------------------------
@@ -264,21 +291,24 @@ __device__ __forceinline__ uint32_t srt_d2q9(const T (&d)[9], T rho0, T omega, T
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, T omega, T (&out)[3]) {
-    const T W0 = T(2.0 / 3.0), W1 = T(1.0 / 6.0);
+    using N = Num<T>;
+    constexpr double W[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
     const T drho = d[0] + d[1] + d[2];
     const T rho = rho0 + drho;
-    const T u = (d[1] - d[2]) * Math<T>::rcp(rho);
-    const T b0 = T(-1.5) * u * u;
-    const T s = T(3) * u * u;  // 9/2 u^2 - 3/2 u^2
-    const T deq0 = W0 * drho + W0 * rho * b0;
-    const T deq1 = W1 * drho + W1 * rho * (s + T(3) * u);
-    const T deq2 = W1 * drho + W1 * rho * (s - T(3) * u);
-    out[0] = d[0] + omega * (deq0 - d[0]);
-    out[1] = d[1] + omega * (deq1 - d[1]);
-    out[2] = d[2] + omega * (deq2 - d[2]);
-    const T fmn = fmin((out[0] + W0 * rho0) * T(1.5),
-                       fmin((out[1] + W1 * rho0) * T(6), (out[2] + W1 * rho0) * T(6)));
-    return (!(fmn >= T(0)) || !isfinite(out[0] + out[1] + out[2])) ? ST_UNSTABLE : 0u;
+    const T u = (d[1] - d[2]) * N::rcp(rho);
+    const T b0 = T(-1.5) * (u * u);
+    const T s = T(3.0) * (u * u);  // 9/2 u^2 - 3/2 u^2
+    const T w0 = T(W[0]), w1 = T(W[1]);
+    const T deq0 = N::mad(w0 * rho, b0, w0 * drho);
+    const T deq1 = N::mad(w1 * rho, N::mad(T(3.0), u, s), w1 * drho);
+    const T deq2 = N::mad(w1 * rho, N::mad(T(-3.0), u, s), w1 * drho);
+    out[0] = N::mad(omega, deq0 - d[0], d[0]);
+    out[1] = N::mad(omega, deq1 - d[1], d[1]);
+    out[2] = N::mad(omega, deq2 - d[2], d[2]);
+    typename N::Pred all;
+    if constexpr (N::LANES == 1) all = true;
+    else all = {true, true};
+    return lane_status<T>(all, finite_nonneg<T, 3>(out, W, rho0));
 }
 
 // Dispatch by lattice and rule.

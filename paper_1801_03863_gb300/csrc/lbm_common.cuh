@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------
@@ -103,6 +105,12 @@ struct TileDesc {
     int32_t pad;
 };
 
+// Opaque 128-byte TMA tensor map as the kernels see it (the host fills it
+// with cuTensorMapEncodeTiled).
+struct alignas(128) CUtensorMapOpaque {
+    uint64_t q[16];
+};
+
 struct StepArgs {
     const void* src;  // populations f^post(t-1) (deviations)
     void* dst;        // populations f^post(t)
@@ -114,6 +122,8 @@ struct StepArgs {
     int32_t th;       // tile height in rows
     double rho0;
     unsigned long long* status;  // [count][2]: newton skipped, unstable
+    const void* tmaps;           // per-instance tensor maps of src (TMA kernel only)
+    unsigned int* error;         // device error word (bounded waits that ran out)
 };
 
 __host__ __device__ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }

@@ -221,48 +221,71 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
             }
         }
 
-        const T omega = (T)in.omega;
+        // Collide nodes one at a time (FP64) or two at a time (FP32, packed
+        // FP32x2 arithmetic).
+        using CT = typename std::conditional<std::is_same<T, float>::value && (V % 2 == 0), F2,
+                                             T>::type;
+        using N = Num<CT>;
+        constexpr int P = N::LANES;
+        const CT omega = CT((typename LaneOf<CT>::type)in.omega);
+        const CT rho0v = CT((typename LaneOf<CT>::type)rho0);
         const bool cavity_edge =
             (bc == BC_CAVITY) && (y == 0 || y == ny - 1 || x0 == 0 || x0 + V >= nx);
         Chunk<S, V> out[Q];
         uint32_t n_skip = 0, n_unst = 0;
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            T d[Q], o[Q];
+        for (int i = 0; i < V; i += P) {
+            CT d[Q], o[Q];
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const int vxa = Lat::vx(a);
-                S s;
-                if (vxa == 0) s = raw[a].get(i);
-                else if (vxa == 1) s = (i == 0) ? left[a] : raw[a].get(i - 1);
-                else s = (i == V - 1) ? right[a] : raw[a].get(i + 1);
-                d[a] = to_compute<T, S>(s);
-            }
-            uint32_t st = Collide<Lat, COLL, T>::run(d, rho0, omega, o);
-            if (cavity_edge) {
-                const int x = x0 + i;
-                const bool wall = (x == 0) || (x == nx - 1) || (y == 0);
-                const bool lid = !wall && (y == ny - 1);
-                if (wall) {
-                    // full-way bounce-back: reverse every population (W_opp = W_a)
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) o[a] = d[Lat::opp(a)];
-                    st = 0;
-                } else if (lid) {
-#pragma unroll
-                    for (int a = 0; a < Q; ++a) {
-                        if constexpr (std::is_same<T, double>::value) o[a] = in.lid_dev[a];
-                        else o[a] = in.lid_dev_f[a];
-                    }
-                    st = 0;
+                for (int l = 0; l < P; ++l) {
+                    const int j = i + l;
+                    S s;
+                    if (vxa == 0) s = raw[a].get(j);
+                    else if (vxa == 1) s = (j == 0) ? left[a] : raw[a].get(j - 1);
+                    else s = (j == V - 1) ? right[a] : raw[a].get(j + 1);
+                    if constexpr (P == 1) d[a] = to_compute<T, S>(s);
+                    else N::set_lane(d[a], l, to_compute<float, S>(s));
                 }
             }
-            if (x0 + i < nx) {
-                n_skip += st & ST_NEWTON_SKIPPED;
-                n_unst += (st & ST_UNSTABLE) >> 1;
+            uint32_t st = Collide<Lat, COLL, CT>::run(d, rho0v, omega, o);
+            if (cavity_edge) {
+#pragma unroll
+                for (int l = 0; l < P; ++l) {
+                    const int x = x0 + i + l;
+                    const bool wall = (x == 0) || (x == nx - 1) || (y == 0);
+                    const bool lid = !wall && (y == ny - 1);
+                    if (wall) {
+                        // full-way bounce-back: reverse every population (W_opp = W_a)
+#pragma unroll
+                        for (int a = 0; a < Q; ++a)
+                            N::set_lane(o[a], l, N::lane(d[Lat::opp(a)], l));
+                        st &= ~(3u << (2 * l));
+                    } else if (lid) {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) {
+                            if constexpr (std::is_same<T, double>::value)
+                                N::set_lane(o[a], l, in.lid_dev[a]);
+                            else
+                                N::set_lane(o[a], l, in.lid_dev_f[a]);
+                        }
+                        st &= ~(3u << (2 * l));
+                    }
+                }
             }
 #pragma unroll
-            for (int a = 0; a < Q; ++a) out[a].set(i, Store<S>::from(o[a]));
+            for (int l = 0; l < P; ++l) {
+                if (x0 + i + l < nx) {
+                    n_skip += (st >> (2 * l)) & ST_NEWTON_SKIPPED;
+                    n_unst += ((st >> (2 * l)) & ST_UNSTABLE) >> 1;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+#pragma unroll
+                for (int l = 0; l < P; ++l) out[a].set(i + l, Store<S>::from(N::lane(o[a], l)));
         }
         if (ragged) {
             // keep the row padding at deviation 0

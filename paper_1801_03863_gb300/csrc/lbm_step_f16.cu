@@ -1,6 +1,7 @@
 // lbm_step_f16.cu -- fused step kernels with __half storage and float arithmetic.
 #include "lbm_aux.h"
 #include "lbm_step.cuh"
+#include "lbm_step_smem.cuh"
 
 namespace lbm {
 
@@ -20,6 +21,14 @@ const void* step_kernel_f16(int lattice, int collision, int V) {
         return (const void*)&step_kernel<D1Q3, __half, float, 8, COLL_MINXENT4>;
     }
     return nullptr;
+}
+
+const void* step_kernel_smem_f16(int collision, size_t* smem_bytes) {
+    using TS = SmemTile<__half>;
+    *smem_bytes = TS::SMEM_BYTES;
+    return collision == COLL_SRT
+               ? (const void*)&step_kernel_smem<__half, COLL_SRT, TS::TILE_NODES, TS::STAGES>
+               : (const void*)&step_kernel_smem<__half, COLL_MINXENT4, TS::TILE_NODES, TS::STAGES>;
 }
 
 }  // namespace lbm

@@ -1,0 +1,385 @@
+// lbm_step_smem.cuh -- the D2Q9 step with TMA staging of halo tiles
+// (FP32 collide arithmetic, FP32 / FP16 / BF16 storage).
+//
+// Same time step as step_kernel (pull-stream + collide + boundary rules of
+// Sec. IV.F, Eq. 2), organised around the Tensor Memory Accelerator:
+//
+//  * A CTA (256 threads) walks the tile table of the context; a tile is X
+//    nodes (64, 128 or 256, chosen per instance) by R = TILE_NODES / X rows.
+//  * Each instance's populations are described to TMA as a 4-D tensor
+//    (element within a 16-byte chunk, chunk, row, plane).  For every plane
+//    one elected thread issues a single tensor copy of the tile's rows
+//    shifted by -v_y, one chunk wider on each side in x (the halo); copies
+//    outside the lattice are zero-filled by the hardware, which is exactly
+//    the cavity's "outside" value (deviation 0).
+//  * A two-stage shared-memory ring with one mbarrier per stage: the copies
+//    of tile k+1 are in flight while tile k is collided.  Every wait is
+//    bounded; on timeout the kernel records an error word and the CTA leaves
+//    after a bounded wait for its own copies still in flight.
+//  * Halo values a zero fill cannot express (periodic wrap, zero-gradient
+//    copies of the element beyond an end) are patched in shared memory.
+//  * Each thread collides one node pair per row (packed FP32x2 arithmetic),
+//    reading 4-byte words from shared memory (consecutive threads,
+//    consecutive words: no bank conflicts) and storing each plane's pair
+//    with one 4- or 8-byte store (a warp writes 128 or 256 contiguous bytes).
+#pragma once
+#include "lbm_collide.cuh"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+#ifndef LBM_SMEM_TILE2
+#define LBM_SMEM_TILE2 1024  // nodes per tile, 2-byte storage
+#endif
+#ifndef LBM_SMEM_TILE4
+#define LBM_SMEM_TILE4 512   // nodes per tile, 4-byte storage
+#endif
+#ifndef LBM_SMEM_STAGES
+#define LBM_SMEM_STAGES 3    // depth of the shared-memory ring
+#endif
+
+template <typename S, int TILE = (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4),
+          int NST = LBM_SMEM_STAGES>
+struct SmemTile {
+    static constexpr int E = 16 / (int)sizeof(S);  // elements per 16-byte chunk
+    static constexpr int TILE_NODES = TILE;        // X * R
+    static constexpr int STAGES = NST;             // depth of the shared-memory ring
+    static constexpr int THREADS = 256;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int MAX_ROWS = TILE_NODES / 64;  // R at X = 64
+    // elements of one plane at the largest smem footprint (X = 64); a
+    // multiple of 64 elements, so every plane region is 128-byte aligned
+    static constexpr int PLANE_ELEMS = TILE_NODES + 2 * E * MAX_ROWS;
+    static constexpr int STAGE_ELEMS = 9 * PLANE_ELEMS;
+    static constexpr size_t STAGES_BYTES = (size_t)STAGES * STAGE_ELEMS * sizeof(S);
+    // + room to round the dynamic base up to 128 bytes, per-stage tile
+    // parameters and two mbarriers per stage
+    static constexpr size_t PARAMS_OFF = STAGES_BYTES;
+    static constexpr size_t BARS_OFF = PARAMS_OFF + 128 * STAGES;
+    static constexpr size_t SMEM_BYTES = 128 + BARS_OFF + 16 * STAGES;
+    static_assert((PLANE_ELEMS * sizeof(S)) % 128 == 0, "plane regions must stay 128-byte aligned");
+};
+
+// Parameters of the tile held by one stage, written by the producing thread
+// before it arms the stage's barrier (consumers read them after the wait).
+struct StageParams {
+    int64_t off, pitch, plane;
+    int32_t inst, X, x0, y0, nx, ny, bc, R;
+    float omega;
+    float lid[9];
+};
+static_assert(sizeof(StageParams) <= 128, "stage parameters must fit 128 bytes");
+
+// Bounded spin limit of one mbarrier wait (each try_wait may itself suspend
+// for a while); a copy that has not landed by then is treated as lost.
+constexpr int MBAR_SPIN_LIMIT = 1 << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                            int c3, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Pair of nodes (2p, 2p+1) of one plane as FP32x2.  `row` points at the
+// shared-memory row of the plane; `wb` is the index (in 32-bit words for
+// 2-byte types, in elements for FP32) of the pair's own position, element
+// E + 2p.  The pull shift -v_x is a compile-time offset from it.
+template <typename S, int VX>
+__device__ __forceinline__ float2 smem_pair(const S* row, int wb) {
+    if constexpr (sizeof(S) == 2) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(row) + wb;
+        uint32_t v;
+        if constexpr (VX == 0) v = w[0];
+        else if constexpr (VX == 1) v = __byte_perm(w[-1], w[0], 0x5432);  // elements 2p-1, 2p
+        else v = __byte_perm(w[0], w[1], 0x5432);                           // elements 2p+1, 2p+2
+        if constexpr (std::is_same<S, __half>::value) {
+            return __half22float2(*reinterpret_cast<const __half2*>(&v));
+        } else {
+            return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
+        }
+    } else {
+        const float* f = reinterpret_cast<const float*>(row) + wb - VX;
+        return make_float2(f[0], f[1]);
+    }
+}
+
+// Store one pair (lane 1 dropped when it lies beyond the row: padding stays 0).
+template <typename S>
+__device__ __forceinline__ void store_pair(S* p, float a, float b, bool second_valid) {
+    if (!second_valid) b = 0.f;
+    if constexpr (std::is_same<S, __half>::value) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    } else {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+}
+
+__device__ __forceinline__ int wrap_index(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Pair of nodes (x, x+1) of row y pulled straight from global memory with
+// the periodic (wrap) or zero-gradient (x clamp, y wrap) rule: used by the
+// nodes of periodic / zero-gradient lattices whose pull crosses an edge,
+// where the zero-filled tile halo does not hold the boundary value.
+template <typename S>
+__device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int nx, int ny, int bc,
+                                              int x, int y, int vx, int vy) {
+    const int sy = wrap_index(y - vy, ny);
+    int xa = x - vx, xb = x + 1 - vx;
+    if (bc == BC_PERIODIC) {
+        xa = wrap_index(xa, nx);
+        xb = wrap_index(xb, nx);
+    } else {
+        xa = min(max(xa, 0), nx - 1);
+        xb = min(max(xb, 0), nx - 1);
+    }
+    const S* row = base + (int64_t)sy * pitch;
+    return make_float2(to_compute<float, S>(row[xa]), to_compute<float, S>(row[xb]));
+}
+
+#ifndef LBM_SMEM_MINBLOCKS
+#define LBM_SMEM_MINBLOCKS 2  // resident CTAs per SM the register budget aims at
+#endif
+
+template <typename S, int COLL, int TILE, int NST>
+__global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(const StepArgs args) {
+    using TS = SmemTile<S, TILE, NST>;
+    constexpr int E = TS::E;
+    constexpr int Q = 9;
+    constexpr int NS = TS::STAGES;
+    using N = Num<F2>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations must be 16-byte (here: 128-byte) aligned: round the
+    // dynamic base up explicitly.  Layout: stages | stage parameters |
+    // full barriers | empty barriers.
+    unsigned char* smem_al = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    S* stage_base = reinterpret_cast<S*>(smem_al);
+    StageParams* params = reinterpret_cast<StageParams*>(smem_al + TS::PARAMS_OFF);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_al + TS::BARS_OFF);
+    uint64_t* empty = full + NS;
+    const S* __restrict__ src = static_cast<const S*>(args.src);
+    S* __restrict__ dst = static_cast<S*>(args.dst);
+    const CUtensorMapOpaque* tmaps = static_cast<const CUtensorMapOpaque*>(args.tmaps);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const F2 rho0v = F2((float)args.rho0);
+    const int G = gridDim.x;
+    // local tile j of this CTA is global tile blockIdx.x + j * G
+    const int ntl = (args.ntiles > (int)blockIdx.x) ? (args.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
+
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], TS::WARPS);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // Thread 0 fills stage j % NS with local tile j: parameters, then the
+    // nine plane copies on the stage's full barrier.  Returns false if the
+    // stage was not released in time.
+    auto produce = [&](int j) -> bool {
+        const int st = j % NS, fill = j / NS;
+        if (fill > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((fill - 1) & 1))) return false;
+        const TileDesc tile = args.tiles[blockIdx.x + j * G];
+        const InstDesc& in = args.inst[tile.inst];
+        StageParams& p = params[st];
+        p.off = in.off; p.pitch = in.pitch; p.plane = in.plane;
+        p.inst = tile.inst; p.X = tile.pad; p.x0 = tile.cx0; p.y0 = tile.y0;
+        p.nx = in.nx; p.ny = in.ny; p.bc = in.bc; p.R = TS::TILE_NODES / tile.pad;
+        p.omega = (float)in.omega;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) p.lid[a] = in.lid_dev_f[a];
+        const uint32_t bytes = (uint32_t)(Q * p.R * (p.X + 2 * E) * sizeof(S));
+        S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
+        const void* map = &tmaps[tile.inst];
+        fence_proxy_async_smem();  // consumers' reads of this stage come first
+        mbar_arrive_expect_tx(&full[st], bytes);
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            tma_load_4d(sbase + a * TS::PLANE_ELEMS, map, 0, tile.cx0 / E - 1,
+                        tile.y0 - D2Q9::vy(a), a, &full[st]);
+        return true;
+    };
+
+    bool fail = false;
+    int issued = 0;  // local tiles handed to TMA (thread 0's count)
+    int jdone = -1;  // last local tile whose copies this thread saw land
+    if (tid == 0) {
+        for (; issued < min(NS - 1, ntl); ++issued)
+            if (!produce(issued)) { fail = true; break; }
+    }
+    for (int j = 0; j < ntl && !fail; ++j) {
+        const int st = j % NS;
+        // keep NS - 1 tiles in flight: refill the stage released by tile j - 1
+        if (tid == 0 && issued < ntl && issued == j + NS - 1) {
+            if (produce(issued)) ++issued;
+            else fail = true;
+        }
+        if (!mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1))) fail = true;
+        if (fail) break;
+        jdone = j;
+
+        const StageParams& p = params[st];
+        const int X = p.X, R = p.R;
+        const int SP = X + 2 * E;  // smem row length (elements)
+        const int x0 = p.x0, y0 = p.y0, nx = p.nx, ny = p.ny, bc = p.bc;
+        const int64_t pitch = p.pitch, plane = p.plane, off = p.off;
+        S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
+
+        const int pcols = X >> 1;                 // node pairs per row
+        const int px = tid & (pcols - 1);
+        const int rg = tid / pcols;               // first row of this thread
+        const int rstep = TS::THREADS / pcols;    // rows between this thread's pairs
+        const int x = x0 + 2 * px;
+        // own position of the pair in a shared row: element E + 2 px
+        const int wb = (sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px);
+        const F2 omega = F2(p.omega);
+        uint32_t n_skip = 0, n_unst = 0;
+        const bool second = (x + 1 < nx);
+        const bool xedge = (x == 0) || (x + 1 >= nx - 1);
+        const bool xin = x < nx;
+        constexpr int MAXP = TS::TILE_NODES / (2 * TS::THREADS);  // pairs per thread
+        float lid[Q];
+        if (bc == BC_CAVITY) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) lid[a] = p.lid[a];
+        }
+        const int inst = p.inst;
+#ifdef LBM_SMEM_INTERLEAVE
+#pragma unroll
+#else
+#pragma unroll 1
+#endif
+        for (int k = 0; k < MAXP; ++k) {
+            const int r = rg + k * rstep;
+            const int y = y0 + r;
+            F2 d[Q];
+            {
+                const S* srow = sbase + r * SP;
+                d[0] = F2(smem_pair<S, 0>(srow + 0 * TS::PLANE_ELEMS, wb));
+                d[1] = F2(smem_pair<S, 1>(srow + 1 * TS::PLANE_ELEMS, wb));
+                d[2] = F2(smem_pair<S, 0>(srow + 2 * TS::PLANE_ELEMS, wb));
+                d[3] = F2(smem_pair<S, -1>(srow + 3 * TS::PLANE_ELEMS, wb));
+                d[4] = F2(smem_pair<S, 0>(srow + 4 * TS::PLANE_ELEMS, wb));
+                d[5] = F2(smem_pair<S, 1>(srow + 5 * TS::PLANE_ELEMS, wb));
+                d[6] = F2(smem_pair<S, -1>(srow + 6 * TS::PLANE_ELEMS, wb));
+                d[7] = F2(smem_pair<S, -1>(srow + 7 * TS::PLANE_ELEMS, wb));
+                d[8] = F2(smem_pair<S, 1>(srow + 8 * TS::PLANE_ELEMS, wb));
+            }
+            if (y >= ny || !xin) continue;
+            if (bc != BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
+                const S* gb = src + off;
+#pragma unroll
+                for (int a = 0; a < Q; ++a)
+                    d[a] = F2(global_pair<S>(gb + a * plane, pitch, nx, ny, bc, x, y, D2Q9::vx(a),
+                                             D2Q9::vy(a)));
+            }
+            F2 o[Q];
+            uint32_t sts = Collide<D2Q9, COLL, F2>::run(d, rho0v, omega, o);
+            if (bc == BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    const int xl2 = x + l;
+                    const bool wall = (xl2 == 0) || (xl2 == nx - 1) || (y == 0);
+                    const bool lidn = !wall && (y == ny - 1);
+                    if (wall) {
+                        // full-way bounce-back of the pulled populations, re-read
+                        // from the stage so they need not stay live through the
+                        // collision (the stage is released after the tile)
+                        const S* srow = sbase + r * SP;
+                        float2 v[Q];
+                        v[0] = smem_pair<S, 0>(srow + 0 * TS::PLANE_ELEMS, wb);
+                        v[1] = smem_pair<S, 1>(srow + 1 * TS::PLANE_ELEMS, wb);
+                        v[2] = smem_pair<S, 0>(srow + 2 * TS::PLANE_ELEMS, wb);
+                        v[3] = smem_pair<S, -1>(srow + 3 * TS::PLANE_ELEMS, wb);
+                        v[4] = smem_pair<S, 0>(srow + 4 * TS::PLANE_ELEMS, wb);
+                        v[5] = smem_pair<S, 1>(srow + 5 * TS::PLANE_ELEMS, wb);
+                        v[6] = smem_pair<S, -1>(srow + 6 * TS::PLANE_ELEMS, wb);
+                        v[7] = smem_pair<S, -1>(srow + 7 * TS::PLANE_ELEMS, wb);
+                        v[8] = smem_pair<S, 1>(srow + 8 * TS::PLANE_ELEMS, wb);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) {
+                            const float2 w = v[D2Q9::opp(a)];
+                            N::set_lane(o[a], l, l ? w.y : w.x);
+                        }
+                        sts &= ~(3u << (2 * l));
+                    } else if (lidn) {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) N::set_lane(o[a], l, lid[a]);
+                        sts &= ~(3u << (2 * l));
+                    }
+                }
+            }
+            if (!second) sts &= 3u;
+            n_skip += (sts & ST_NEWTON_SKIPPED) + ((sts >> 2) & ST_NEWTON_SKIPPED);
+            n_unst += ((sts & ST_UNSTABLE) >> 1) + (((sts >> 2) & ST_UNSTABLE) >> 1);
+            S* op = dst + off + (int64_t)y * pitch + x;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                store_pair<S>(op, o[a].v.x, o[a].v.y, second);
+                op += plane;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
+        if (n_skip | n_unst) {
+            atomicAdd(args.status + 2 * inst + 0, (unsigned long long)n_skip);
+            atomicAdd(args.status + 2 * inst + 1, (unsigned long long)n_unst);
+        }
+    }
+    if (fail) {
+        // a copy or a stage release never came: report it and give this
+        // CTA's copies still in flight a bounded chance to land before exit
+        atomicOr(args.error, 1u);
+        if (tid == 0) {
+            for (int j = jdone + 1; j < issued; ++j)
+                mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1));
+        }
+    }
+}
+
+}  // namespace lbm

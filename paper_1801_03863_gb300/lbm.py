@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_ALLOC, LBM_ERR_CUDA = 0, -1, -2, -3
-LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NODEV = -4, -5, -6
+LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NODEV, LBM_ERR_TIMEOUT = -4, -5, -6, -7
 LBM_D1Q3, LBM_D2Q9 = 1, 2
 LBM_BC_PERIODIC, LBM_BC_ZERO_GRADIENT, LBM_BC_CAVITY = 0, 1, 2
 LBM_MINXENT4, LBM_SRT = 0, 1
@@ -225,9 +225,10 @@ def lbm_status_instance(h, i: int) -> dict:
 
 
 def lbm_launch_shape(h) -> dict:
-    c = np.zeros(4, np.int32)
+    c = np.zeros(5, np.int32)
     _check(load().lbm_launch_shape(h, _p(c)), "lbm_launch_shape")
-    return {"V": int(c[0]), "tw": int(c[1]), "th": int(c[2]), "grid": int(c[3])}
+    return {"V": int(c[0]), "tw": int(c[1]), "th": int(c[2]), "grid": int(c[3]),
+            "kind": "smem" if c[4] == 1 else "chunks"}
 
 
 def lbm_destroy(h) -> None:

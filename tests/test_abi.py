@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         s = lbm.lbm_status_string(code)
         assert s and "unknown" not in s
     assert "unknown" in lbm.lbm_status_string(-99)

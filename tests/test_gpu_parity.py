@@ -239,13 +239,18 @@ def test_launch_shapes_agree_bitwise(storage, monkeypatch):
     nx, ny = 72, 40
     fields = wl.taylor_green(nx, u0=0.05, ny=ny)
     compute = "f64" if storage == "f64" else "f32"
-    shapes = ["2,4,32", "2,16,8", "2,64,4"] if storage == "f64" else ["4,8,16", "8,4,32", "8,32,8"]
+    shapes = ["2,4,32", "2,16,8", "2,64,4"] if storage == "f64" else \
+        ["4,8,16", "8,4,32", "8,32,8", "smem"]
     ref = None
     for s in shapes:
         monkeypatch.setenv("LBM_SHAPE", s)
         with lbm.Lattice("d2q9", [(nx, ny)], 0.01, "periodic", compute=compute,
                          storage=storage) as lat:
-            assert lat.launch_shape()["V"] == int(s.split(",")[0])
+            sh = lat.launch_shape()
+            if s == "smem":
+                assert sh["kind"] == "smem"
+            else:
+                assert sh["V"] == int(s.split(",")[0]) and sh["kind"] == "chunks"
             lat.init(*fields)
             lat.step(37)
             f = lat.populations()
@@ -253,6 +258,34 @@ def test_launch_shapes_agree_bitwise(storage, monkeypatch):
             ref = f
         else:
             assert np.array_equal(f, ref), s
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("bc,dims", [("periodic", [(37, 29)]), ("periodic", [(300, 9)]),
+                                     ("cavity", [(70, 50)]), ("cavity", [(133, 133), (64, 64)]),
+                                     ("zero_gradient", [(45, 23)]), ("zero_gradient", [(264, 5)])])
+def test_smem_kernel_matches_chunk_kernel(storage, bc, dims, monkeypatch):
+    """The shared-memory staged kernel and the register-chunk kernel run the
+    same FP32 arithmetic in the same order, so they agree bit for bit, over
+    ragged widths, multi-tile rows, every boundary kind and ensembles."""
+    nus = [0.01 + 0.002 * i for i in range(len(dims))]
+    f0 = np.concatenate([wl.random_populations(9, ny, nx, eps=0.2, seed=3 + i).reshape(9, -1)
+                         for i, (nx, ny) in enumerate(dims)], axis=1)
+    # per-instance [a][y][x] blocks, concatenated
+    parts, k = [], 0
+    for nx, ny in dims:
+        parts.append(f0[:, k:k + nx * ny].ravel())
+        k += nx * ny
+    f0 = np.concatenate(parts)
+    out = {}
+    for s in ("4,8,16", "smem"):
+        monkeypatch.setenv("LBM_SHAPE", s if storage != "f32" else ("2,16,8" if s != "smem" else s))
+        with lbm.Lattice("d2q9", dims, nus, bc, u_lid=0.07, compute="f32", storage=storage) as lat:
+            lat.set_populations(f0)
+            lat.step(21)
+            out[s] = (lat.populations(), lat.status())
+    assert out["smem"][1] == out["4,8,16"][1]
+    assert np.array_equal(out["smem"][0], out["4,8,16"][0])
 
 
 def test_unstable_node_is_reported():
@@ -335,8 +368,9 @@ def test_reduced_precision_taylor_green(storage):
     assert np.abs(r - ro).max() <= bound_r, np.abs(r - ro).max()
 
 
+@pytest.mark.parametrize("shape", ["auto", "smem"])
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-def test_reduced_precision_one_step_every_node(storage):
+def test_reduced_precision_one_step_every_node(storage, shape, monkeypatch):
     """One step from an FP16-representable state: the only differences are
     FP32 arithmetic and the final rounding of each deviation to storage."""
     nx, ny = 64, 24
@@ -347,6 +381,8 @@ def test_reduced_precision_one_step_every_node(storage):
     dev0 = f0 - w
     dev0 = torch.tensor(dev0).to(torch.bfloat16).to(torch.float64).numpy()
     f0 = w + dev0
+    if shape == "smem":
+        monkeypatch.setenv("LBM_SHAPE", "smem")
     with lbm.Lattice("d2q9", [(nx, ny)], 0.02, "periodic", compute="f32", storage=storage) as lat:
         lat.set_populations(f0)
         lat.step(1)
