@@ -42,7 +42,10 @@ std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, in
     else if (storage == DT_F32) vs = {2, 4};
     else vs = {4, 8};
     std::vector<Shape> out;
-    if (lattice == 2 && storage != DT_F64) out.push_back({2, 0, 0, 1});
+    if (lattice == 2 && storage != DT_F64) {
+        out.push_back({2, 0, 0, 1});  // shared-memory staged kernel, node pairs
+        out.push_back({1, 0, 0, 1});  // shared-memory staged kernel, single nodes
+    }
     for (int V : vs) {
         for (int block : {128, 256}) {
             for (int tw = 4; tw <= block; tw *= 2) {
@@ -263,9 +266,9 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     size_t smem = 0;
     if (s.kind == 1) {
         if (ctx->lattice != 2 || ctx->compute != DT_F32) return LBM_ERR_ARG;
-        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, &smem);
-        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, &smem);
-        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, &smem);
+        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, s.V, &smem);
+        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, s.V, &smem);
+        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, s.V, &smem);
         if (!k) return LBM_ERR_ARG;
         LBM_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int rc = build_tensor_maps(ctx);
@@ -414,8 +417,12 @@ int autotune(lbm_ctx* ctx) {
 bool parse_shape_env(Shape* s) {
     const char* e = getenv("LBM_SHAPE");
     if (!e) return false;
-    if (strcmp(e, "smem") == 0) {
+    if (strcmp(e, "smem") == 0 || strcmp(e, "smem2") == 0) {
         *s = {2, 0, 0, 1};
+        return true;
+    }
+    if (strcmp(e, "smem1") == 0) {
+        *s = {1, 0, 0, 1};
         return true;
     }
     int v, tw, th;

@@ -90,6 +90,7 @@ __global__ void set_f_kernel(S* dst, const InstDesc* insts, const double* f, dou
 template <class Lat, typename S, typename T, int COLL>
 __global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* insts, double rho0,
                                        unsigned long long* status) {
+    using CT = typename std::conditional<std::is_same<T, float>::value, F1, T>::type;
     const int inst = blockIdx.y;
     const InstDesc& in = insts[inst];
     const int64_t n = (int64_t)in.nx * in.ny;
@@ -97,14 +98,14 @@ __global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* ins
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(k % in.nx), y = (int)(k / in.nx);
-        T d[Lat::Q], o[Lat::Q];
+        CT d[Lat::Q], o[Lat::Q];
 #pragma unroll
         for (int a = 0; a < Lat::Q; ++a) {
             const S v = *elem_ptr<Lat, S>(src, in, a, x, y);
             if constexpr (std::is_same<T, double>::value) d[a] = Store<S>::to_f64(v);
-            else d[a] = Store<S>::to_f32(v);
+            else d[a] = CT(Store<S>::to_f32(v));
         }
-        uint32_t st = Collide<Lat, COLL, T>::run(d, (T)rho0, (T)in.omega, o);
+        uint32_t st = Collide<Lat, COLL, CT>::run(d, CT((T)rho0), CT((T)in.omega), o);
         if (in.bc == BC_CAVITY) {
             const bool wall = (x == 0) || (x == in.nx - 1) || (y == 0);
             const bool lid = !wall && (y == in.ny - 1);
@@ -114,16 +115,22 @@ __global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* ins
                 st = 0;
             } else if (lid) {
 #pragma unroll
-                for (int a = 0; a < Lat::Q; ++a)
-                    o[a] = std::is_same<T, double>::value ? (T)in.lid_dev[a] : (T)in.lid_dev_f[a];
+                for (int a = 0; a < Lat::Q; ++a) {
+                    if constexpr (std::is_same<T, double>::value) o[a] = in.lid_dev[a];
+                    else o[a] = CT(in.lid_dev_f[a]);
+                }
                 st = 0;
             }
         }
         n_skip += st & ST_NEWTON_SKIPPED;
         n_unst += (st & ST_UNSTABLE) >> 1;
 #pragma unroll
-        for (int a = 0; a < Lat::Q; ++a)
-            dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(o[a]);
+        for (int a = 0; a < Lat::Q; ++a) {
+            if constexpr (std::is_same<T, double>::value)
+                dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(o[a]);
+            else
+                dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(o[a].v);
+        }
     }
     if (n_skip) atomicAdd(status + 2 * inst + 0, n_skip);
     if (n_unst) atomicAdd(status + 2 * inst + 1, n_unst);

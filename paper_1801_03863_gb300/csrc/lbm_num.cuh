@@ -46,6 +46,23 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b) {
 }
 __device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
 
+// Scalar FP32 with the same rounding discipline as F2: every + - * rounds
+// separately (__fadd_rn / __fmul_rn are never contracted into FMAs), and
+// fused operations are explicit (Num<F1>::mad).  Scalar and packed FP32
+// paths therefore give bitwise identical results.
+struct F1 {
+    float v;
+    F1() = default;
+    __device__ __forceinline__ constexpr F1(float a) : v(a) {}
+};
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1(__fadd_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator-(F1 a) { return F1(-a.v); }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1(__fsub_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(__fmul_rn(a.v, b.v)); }
+__device__ __forceinline__ bool operator>=(F1 a, F1 b) { return a.v >= b.v; }
+__device__ __forceinline__ bool operator<(F1 a, F1 b) { return a.v < b.v; }
+__device__ __forceinline__ F1 fabs(F1 a) { return F1(fabsf(a.v)); }
+
 // Per-lane predicate.
 struct B2 {
     bool x, y;
@@ -82,6 +99,20 @@ template <> struct Num<float> {
     __device__ static __forceinline__ void set_lane(float& v, int, float x) { v = x; }
 };
 
+template <> struct Num<F1> {
+    using Pred = bool;
+    static constexpr int LANES = 1;
+    static constexpr float LOG_SCALE = 0.693147180559945309f;  // log returns log2
+    __device__ static __forceinline__ F1 mad(F1 a, F1 b, F1 c) { return F1(__fmaf_rn(a.v, b.v, c.v)); }
+    __device__ static __forceinline__ F1 rcp(F1 x) { return F1(rcp_approx(x.v)); }
+    __device__ static __forceinline__ F1 lnp(F1, F1 y) { return F1(lg2_approx(y.v)); }
+    __device__ static __forceinline__ F1 vmin(F1 a, F1 b) { return F1(fminf(a.v, b.v)); }
+    __device__ static __forceinline__ Pred gt(F1 a, F1 b) { return a.v > b.v; }
+    __device__ static __forceinline__ F1 sel(Pred p, F1 a, F1 b) { return p ? a : b; }
+    __device__ static __forceinline__ float lane(F1 v, int) { return v.v; }
+    __device__ static __forceinline__ void set_lane(F1& v, int, float x) { v.v = x; }
+};
+
 template <> struct Num<F2> {
     using Pred = B2;
     static constexpr int LANES = 2;
@@ -106,5 +137,6 @@ template <> struct Num<F2> {
 // Scalar type of one lane.
 template <typename T> struct LaneOf { using type = T; };
 template <> struct LaneOf<F2> { using type = float; };
+template <> struct LaneOf<F1> { using type = float; };
 
 }  // namespace lbm

@@ -223,8 +223,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
 
         // Collide nodes one at a time (FP64) or two at a time (FP32, packed
         // FP32x2 arithmetic).
-        using CT = typename std::conditional<std::is_same<T, float>::value && (V % 2 == 0), F2,
-                                             T>::type;
+        using CT = typename std::conditional<
+            std::is_same<T, float>::value, typename std::conditional<(V % 2 == 0), F2, F1>::type,
+            T>::type;
         using N = Num<CT>;
         constexpr int P = N::LANES;
         const CT omega = CT((typename LaneOf<CT>::type)in.omega);
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
                     if (vxa == 0) s = raw[a].get(j);
                     else if (vxa == 1) s = (j == 0) ? left[a] : raw[a].get(j - 1);
                     else s = (j == V - 1) ? right[a] : raw[a].get(j + 1);
-                    if constexpr (P == 1) d[a] = to_compute<T, S>(s);
+                    if constexpr (std::is_same<CT, double>::value) d[a] = to_compute<T, S>(s);
                     else N::set_lane(d[a], l, to_compute<float, S>(s));
                 }
             }

@@ -23,12 +23,15 @@ const void* step_kernel_bf16(int lattice, int collision, int V) {
     return nullptr;
 }
 
-const void* step_kernel_smem_bf16(int collision, size_t* smem_bytes) {
+const void* step_kernel_smem_bf16(int collision, int P, size_t* smem_bytes) {
     using TS = SmemTile<__nv_bfloat16>;
     *smem_bytes = TS::SMEM_BYTES;
-    return collision == COLL_SRT
-               ? (const void*)&step_kernel_smem<__nv_bfloat16, COLL_SRT, TS::TILE_NODES, TS::STAGES>
-               : (const void*)&step_kernel_smem<__nv_bfloat16, COLL_MINXENT4, TS::TILE_NODES, TS::STAGES>;
+    constexpr int TN = TS::TILE_NODES, NS = TS::STAGES;
+    if (P == 1)
+        return collision == COLL_SRT ? (const void*)&step_kernel_smem<__nv_bfloat16, COLL_SRT, TN, NS, 1>
+                                     : (const void*)&step_kernel_smem<__nv_bfloat16, COLL_MINXENT4, TN, NS, 1>;
+    return collision == COLL_SRT ? (const void*)&step_kernel_smem<__nv_bfloat16, COLL_SRT, TN, NS, 2>
+                                 : (const void*)&step_kernel_smem<__nv_bfloat16, COLL_MINXENT4, TN, NS, 2>;
 }
 
 }  // namespace lbm

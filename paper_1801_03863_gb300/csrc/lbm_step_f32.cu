@@ -23,12 +23,15 @@ const void* step_kernel_f32(int lattice, int collision, int V) {
     return nullptr;
 }
 
-const void* step_kernel_smem_f32(int collision, size_t* smem_bytes) {
+const void* step_kernel_smem_f32(int collision, int P, size_t* smem_bytes) {
     using TS = SmemTile<float>;
     *smem_bytes = TS::SMEM_BYTES;
-    return collision == COLL_SRT
-               ? (const void*)&step_kernel_smem<float, COLL_SRT, TS::TILE_NODES, TS::STAGES>
-               : (const void*)&step_kernel_smem<float, COLL_MINXENT4, TS::TILE_NODES, TS::STAGES>;
+    constexpr int TN = TS::TILE_NODES, NS = TS::STAGES;
+    if (P == 1)
+        return collision == COLL_SRT ? (const void*)&step_kernel_smem<float, COLL_SRT, TN, NS, 1>
+                                     : (const void*)&step_kernel_smem<float, COLL_MINXENT4, TN, NS, 1>;
+    return collision == COLL_SRT ? (const void*)&step_kernel_smem<float, COLL_SRT, TN, NS, 2>
+                                 : (const void*)&step_kernel_smem<float, COLL_MINXENT4, TN, NS, 2>;
 }
 
 }  // namespace lbm

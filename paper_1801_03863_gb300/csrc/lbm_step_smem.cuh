@@ -142,6 +142,18 @@ __device__ __forceinline__ float2 smem_pair(const S* row, int wb) {
     }
 }
 
+// Single node x of one plane (one-node-per-thread variant): element e - VX.
+template <typename S, int VX>
+__device__ __forceinline__ float smem_elem(const S* row, int e) {
+    return to_compute<float, S>(row[e - VX]);
+}
+
+// Store one node.
+template <typename S>
+__device__ __forceinline__ void store_elem(S* p, float a) {
+    *p = Store<S>::from(a);
+}
+
 // Store one pair (lane 1 dropped when it lies beyond the row: padding stays 0).
 template <typename S>
 __device__ __forceinline__ void store_pair(S* p, float a, float b, bool second_valid) {
@@ -152,6 +164,34 @@ __device__ __forceinline__ void store_pair(S* p, float a, float b, bool second_v
         *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
     } else {
         *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+}
+
+// The nine pulled values of one consumer unit (a node pair, P = 2, or a
+// single node, P = 1) from the stage rows of the current tile row.
+template <typename S, int P, typename CT>
+__device__ __forceinline__ void load_unit(const S* srow, int wb, int plane_elems, CT (&d)[9]) {
+    if constexpr (P == 2) {
+        d[0] = F2(smem_pair<S, 0>(srow + 0 * plane_elems, wb));
+        d[1] = F2(smem_pair<S, 1>(srow + 1 * plane_elems, wb));
+        d[2] = F2(smem_pair<S, 0>(srow + 2 * plane_elems, wb));
+        d[3] = F2(smem_pair<S, -1>(srow + 3 * plane_elems, wb));
+        d[4] = F2(smem_pair<S, 0>(srow + 4 * plane_elems, wb));
+        d[5] = F2(smem_pair<S, 1>(srow + 5 * plane_elems, wb));
+        d[6] = F2(smem_pair<S, -1>(srow + 6 * plane_elems, wb));
+        d[7] = F2(smem_pair<S, -1>(srow + 7 * plane_elems, wb));
+        d[8] = F2(smem_pair<S, 1>(srow + 8 * plane_elems, wb));
+    } else {
+        static_assert(std::is_same<CT, F1>::value, "single nodes use F1");
+        d[0] = smem_elem<S, 0>(srow + 0 * plane_elems, wb);
+        d[1] = smem_elem<S, 1>(srow + 1 * plane_elems, wb);
+        d[2] = smem_elem<S, 0>(srow + 2 * plane_elems, wb);
+        d[3] = smem_elem<S, -1>(srow + 3 * plane_elems, wb);
+        d[4] = smem_elem<S, 0>(srow + 4 * plane_elems, wb);
+        d[5] = smem_elem<S, 1>(srow + 5 * plane_elems, wb);
+        d[6] = smem_elem<S, -1>(srow + 6 * plane_elems, wb);
+        d[7] = smem_elem<S, -1>(srow + 7 * plane_elems, wb);
+        d[8] = smem_elem<S, 1>(srow + 8 * plane_elems, wb);
     }
 }
 
@@ -184,13 +224,21 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
 #define LBM_SMEM_MINBLOCKS 2  // resident CTAs per SM the register budget aims at
 #endif
 
-template <typename S, int COLL, int TILE, int NST>
-__global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(const StepArgs args) {
+#ifndef LBM_SMEM_MINBLOCKS1
+#define LBM_SMEM_MINBLOCKS1 3  // resident CTAs per SM, one-node-per-thread variant
+#endif
+
+// P = nodes per thread and row: 2 (node pairs, packed FP32x2 arithmetic) or
+// 1 (single nodes, scalar FP32, fewer registers and more resident warps).
+template <typename S, int COLL, int TILE, int NST, int P>
+__global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MINBLOCKS1)
+    step_kernel_smem(const StepArgs args) {
     using TS = SmemTile<S, TILE, NST>;
     constexpr int E = TS::E;
     constexpr int Q = 9;
     constexpr int NS = TS::STAGES;
-    using N = Num<F2>;
+    using CT = typename std::conditional<P == 2, F2, F1>::type;
+    using N = Num<CT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations must be 16-byte (here: 128-byte) aligned: round the
     // dynamic base up explicitly.  Layout: stages | stage parameters |
@@ -204,7 +252,7 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(cons
     S* __restrict__ dst = static_cast<S*>(args.dst);
     const CUtensorMapOpaque* tmaps = static_cast<const CUtensorMapOpaque*>(args.tmaps);
     const int tid = threadIdx.x, lane = tid & 31;
-    const F2 rho0v = F2((float)args.rho0);
+    const CT rho0v = CT((float)args.rho0);
     const int G = gridDim.x;
     // local tile j of this CTA is global tile blockIdx.x + j * G
     const int ntl = (args.ntiles > (int)blockIdx.x) ? (args.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -270,19 +318,20 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(cons
         const int64_t pitch = p.pitch, plane = p.plane, off = p.off;
         S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
 
-        const int pcols = X >> 1;                 // node pairs per row
+        const int pcols = X / P;                  // thread columns per row
         const int px = tid & (pcols - 1);
         const int rg = tid / pcols;               // first row of this thread
-        const int rstep = TS::THREADS / pcols;    // rows between this thread's pairs
-        const int x = x0 + 2 * px;
-        // own position of the pair in a shared row: element E + 2 px
-        const int wb = (sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px);
-        const F2 omega = F2(p.omega);
+        const int rstep = TS::THREADS / pcols;    // rows between this thread's units
+        const int x = x0 + P * px;
+        // own position in a shared row: element E + P px (in words for pairs
+        // of 2-byte types)
+        const int wb = (P == 1) ? (E + px) : ((sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px));
+        const CT omega = CT(p.omega);
         uint32_t n_skip = 0, n_unst = 0;
-        const bool second = (x + 1 < nx);
-        const bool xedge = (x == 0) || (x + 1 >= nx - 1);
+        const bool second = (P == 2) && (x + 1 < nx);
+        const bool xedge = (x == 0) || (x + P - 1 >= nx - 1);
         const bool xin = x < nx;
-        constexpr int MAXP = TS::TILE_NODES / (2 * TS::THREADS);  // pairs per thread
+        constexpr int MAXP = TS::TILE_NODES / (P * TS::THREADS);  // units per thread
         float lid[Q];
         if (bc == BC_CAVITY) {
 #pragma unroll
@@ -297,32 +346,27 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(cons
         for (int k = 0; k < MAXP; ++k) {
             const int r = rg + k * rstep;
             const int y = y0 + r;
-            F2 d[Q];
+            CT d[Q];
             {
                 const S* srow = sbase + r * SP;
-                d[0] = F2(smem_pair<S, 0>(srow + 0 * TS::PLANE_ELEMS, wb));
-                d[1] = F2(smem_pair<S, 1>(srow + 1 * TS::PLANE_ELEMS, wb));
-                d[2] = F2(smem_pair<S, 0>(srow + 2 * TS::PLANE_ELEMS, wb));
-                d[3] = F2(smem_pair<S, -1>(srow + 3 * TS::PLANE_ELEMS, wb));
-                d[4] = F2(smem_pair<S, 0>(srow + 4 * TS::PLANE_ELEMS, wb));
-                d[5] = F2(smem_pair<S, 1>(srow + 5 * TS::PLANE_ELEMS, wb));
-                d[6] = F2(smem_pair<S, -1>(srow + 6 * TS::PLANE_ELEMS, wb));
-                d[7] = F2(smem_pair<S, -1>(srow + 7 * TS::PLANE_ELEMS, wb));
-                d[8] = F2(smem_pair<S, 1>(srow + 8 * TS::PLANE_ELEMS, wb));
+                load_unit<S, P>(srow, wb, TS::PLANE_ELEMS, d);
             }
             if (y >= ny || !xin) continue;
             if (bc != BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
                 const S* gb = src + off;
 #pragma unroll
-                for (int a = 0; a < Q; ++a)
-                    d[a] = F2(global_pair<S>(gb + a * plane, pitch, nx, ny, bc, x, y, D2Q9::vx(a),
-                                             D2Q9::vy(a)));
+                for (int a = 0; a < Q; ++a) {
+                    const float2 g = global_pair<S>(gb + a * plane, pitch, nx, ny, bc, x, y,
+                                                    D2Q9::vx(a), D2Q9::vy(a));
+                    if constexpr (P == 2) d[a] = F2(g);
+                    else d[a] = F1(g.x);
+                }
             }
-            F2 o[Q];
-            uint32_t sts = Collide<D2Q9, COLL, F2>::run(d, rho0v, omega, o);
+            CT o[Q];
+            uint32_t sts = Collide<D2Q9, COLL, CT>::run(d, rho0v, omega, o);
             if (bc == BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
 #pragma unroll
-                for (int l = 0; l < 2; ++l) {
+                for (int l = 0; l < P; ++l) {
                     const int xl2 = x + l;
                     const bool wall = (xl2 == 0) || (xl2 == nx - 1) || (y == 0);
                     const bool lidn = !wall && (y == ny - 1);
@@ -331,21 +375,10 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(cons
                         // from the stage so they need not stay live through the
                         // collision (the stage is released after the tile)
                         const S* srow = sbase + r * SP;
-                        float2 v[Q];
-                        v[0] = smem_pair<S, 0>(srow + 0 * TS::PLANE_ELEMS, wb);
-                        v[1] = smem_pair<S, 1>(srow + 1 * TS::PLANE_ELEMS, wb);
-                        v[2] = smem_pair<S, 0>(srow + 2 * TS::PLANE_ELEMS, wb);
-                        v[3] = smem_pair<S, -1>(srow + 3 * TS::PLANE_ELEMS, wb);
-                        v[4] = smem_pair<S, 0>(srow + 4 * TS::PLANE_ELEMS, wb);
-                        v[5] = smem_pair<S, 1>(srow + 5 * TS::PLANE_ELEMS, wb);
-                        v[6] = smem_pair<S, -1>(srow + 6 * TS::PLANE_ELEMS, wb);
-                        v[7] = smem_pair<S, -1>(srow + 7 * TS::PLANE_ELEMS, wb);
-                        v[8] = smem_pair<S, 1>(srow + 8 * TS::PLANE_ELEMS, wb);
+                        CT v[Q];
+                        load_unit<S, P>(srow, wb, TS::PLANE_ELEMS, v);
 #pragma unroll
-                        for (int a = 0; a < Q; ++a) {
-                            const float2 w = v[D2Q9::opp(a)];
-                            N::set_lane(o[a], l, l ? w.y : w.x);
-                        }
+                        for (int a = 0; a < Q; ++a) N::set_lane(o[a], l, N::lane(v[D2Q9::opp(a)], l));
                         sts &= ~(3u << (2 * l));
                     } else if (lidn) {
 #pragma unroll
@@ -357,11 +390,21 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS) step_kernel_smem(cons
             if (!second) sts &= 3u;
             n_skip += (sts & ST_NEWTON_SKIPPED) + ((sts >> 2) & ST_NEWTON_SKIPPED);
             n_unst += ((sts & ST_UNSTABLE) >> 1) + (((sts >> 2) & ST_UNSTABLE) >> 1);
+            if constexpr (P == 1) {
+                S* op1 = dst + off + (int64_t)y * pitch + x;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    store_elem<S>(op1, o[a].v);
+                    op1 += plane;
+                }
+                continue;
+            } else {
             S* op = dst + off + (int64_t)y * pitch + x;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 store_pair<S>(op, o[a].v.x, o[a].v.y, second);
                 op += plane;
+            }
             }
         }
         __syncwarp();

@@ -240,15 +240,15 @@ def test_launch_shapes_agree_bitwise(storage, monkeypatch):
     fields = wl.taylor_green(nx, u0=0.05, ny=ny)
     compute = "f64" if storage == "f64" else "f32"
     shapes = ["2,4,32", "2,16,8", "2,64,4"] if storage == "f64" else \
-        ["4,8,16", "8,4,32", "8,32,8", "smem"]
+        ["4,8,16", "8,4,32", "8,32,8", "smem", "smem1"]
     ref = None
     for s in shapes:
         monkeypatch.setenv("LBM_SHAPE", s)
         with lbm.Lattice("d2q9", [(nx, ny)], 0.01, "periodic", compute=compute,
                          storage=storage) as lat:
             sh = lat.launch_shape()
-            if s == "smem":
-                assert sh["kind"] == "smem"
+            if s.startswith("smem"):
+                assert sh["kind"] == "smem" and sh["V"] == (1 if s == "smem1" else 2)
             else:
                 assert sh["V"] == int(s.split(",")[0]) and sh["kind"] == "chunks"
             lat.init(*fields)
@@ -278,14 +278,15 @@ def test_smem_kernel_matches_chunk_kernel(storage, bc, dims, monkeypatch):
         k += nx * ny
     f0 = np.concatenate(parts)
     out = {}
-    for s in ("4,8,16", "smem"):
-        monkeypatch.setenv("LBM_SHAPE", s if storage != "f32" else ("2,16,8" if s != "smem" else s))
+    for s in ("4,8,16", "smem", "smem1"):
+        monkeypatch.setenv("LBM_SHAPE", s if storage != "f32" or s.startswith("smem") else "2,16,8")
         with lbm.Lattice("d2q9", dims, nus, bc, u_lid=0.07, compute="f32", storage=storage) as lat:
             lat.set_populations(f0)
             lat.step(21)
             out[s] = (lat.populations(), lat.status())
-    assert out["smem"][1] == out["4,8,16"][1]
-    assert np.array_equal(out["smem"][0], out["4,8,16"][0])
+    for s in ("smem", "smem1"):
+        assert out[s][1] == out["4,8,16"][1], s
+        assert np.array_equal(out[s][0], out["4,8,16"][0]), s
 
 
 def test_unstable_node_is_reported():
@@ -368,7 +369,7 @@ def test_reduced_precision_taylor_green(storage):
     assert np.abs(r - ro).max() <= bound_r, np.abs(r - ro).max()
 
 
-@pytest.mark.parametrize("shape", ["auto", "smem"])
+@pytest.mark.parametrize("shape", ["auto", "smem", "smem1"])
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_reduced_precision_one_step_every_node(storage, shape, monkeypatch):
     """One step from an FP16-representable state: the only differences are
@@ -381,8 +382,8 @@ def test_reduced_precision_one_step_every_node(storage, shape, monkeypatch):
     dev0 = f0 - w
     dev0 = torch.tensor(dev0).to(torch.bfloat16).to(torch.float64).numpy()
     f0 = w + dev0
-    if shape == "smem":
-        monkeypatch.setenv("LBM_SHAPE", "smem")
+    if shape != "auto":
+        monkeypatch.setenv("LBM_SHAPE", shape)
     with lbm.Lattice("d2q9", [(nx, ny)], 0.02, "periodic", compute="f32", storage=storage) as lat:
         lat.set_populations(f0)
         lat.step(1)
