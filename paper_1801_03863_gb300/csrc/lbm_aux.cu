@@ -177,10 +177,37 @@ __global__ void gather_f_kernel(const S* src, const InstDesc* insts, bool pulled
     }
 }
 
+// Deviations of f(x, t_n) at one node in FP32 (2- and 4-byte storage):
+// same pull rule as node_state.
+template <class Lat, typename S>
+__device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, bool pulled,
+                               float (&d)[Lat::Q]) {
+#pragma unroll
+    for (int a = 0; a < Lat::Q; ++a) {
+        int sx = x, sy = y;
+        bool inside = true;
+        if (pulled) {
+            sx = x - Lat::vx(a);
+            sy = y - Lat::vy(a);
+            if (in.bc == BC_CAVITY) {
+                inside = sx >= 0 && sx < in.nx && sy >= 0 && sy < in.ny;
+            } else {
+                if (in.bc == BC_PERIODIC) sx = (sx + in.nx) % in.nx;
+                else sx = sx < 0 ? 0 : (sx >= in.nx ? in.nx - 1 : sx);
+                sy = (sy + in.ny) % in.ny;
+            }
+        }
+        d[a] = inside ? Store<S>::to_f32(*elem_ptr<Lat, S>(base, in, a, sx, sy)) : 0.f;
+    }
+}
+
 // Conservation, pass 1: block b of instance i sums (sum d, sum d v_x,
-// sum d v_y) over nodes k = b*256 + t + j*P*256 in FP64 and reduces the
-// block in a fixed tree; partials[(i*P + b)*3 + c].  The grid (P blocks per
-// instance) is a constant, so the summation order is fixed.
+// sum d v_y) over nodes k = b*256 + t + j*P*256 and reduces the block in a
+// fixed tree; partials[(i*P + b)*3 + c].  The grid (P blocks per instance)
+// is a constant, so the summation order is fixed.  The node-level sums of
+// 2- and 4-byte storage run in FP32 (nine deviations of that precision; the
+// rounding of these small sums is far below the stored values' own), every
+// sum across nodes runs in FP64.
 template <class Lat, typename S>
 __global__ void __launch_bounds__(AUX_THREADS)
 cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* partials) {
@@ -191,13 +218,28 @@ cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* pa
     for (int64_t k = (int64_t)blockIdx.x * AUX_THREADS + threadIdx.x; k < n;
          k += (int64_t)CONS_PARTIALS * AUX_THREADS) {
         const int x = (int)(k % in.nx), y = (int)(k / in.nx);
-        double d[Lat::Q];
-        node_state<Lat, S>(src, in, x, y, pulled, d);
+        if constexpr (std::is_same<S, double>::value) {
+            double d[Lat::Q];
+            node_state<Lat, S>(src, in, x, y, pulled, d);
 #pragma unroll
-        for (int a = 0; a < Lat::Q; ++a) {
-            s0 += d[a];
-            s1 += Lat::vx(a) * d[a];
-            s2 += Lat::vy(a) * d[a];
+            for (int a = 0; a < Lat::Q; ++a) {
+                s0 += d[a];
+                s1 += Lat::vx(a) * d[a];
+                s2 += Lat::vy(a) * d[a];
+            }
+        } else {
+            float d[Lat::Q];
+            node_state_f32<Lat, S>(src, in, x, y, pulled, d);
+            float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < Lat::Q; ++a) {
+                r0 += d[a];
+                if (Lat::vx(a) != 0) r1 += (float)Lat::vx(a) * d[a];
+                if (Lat::vy(a) != 0) r2 += (float)Lat::vy(a) * d[a];
+            }
+            s0 += (double)r0;
+            s1 += (double)r1;
+            s2 += (double)r2;
         }
     }
     sh[0][threadIdx.x] = s0;

@@ -85,6 +85,26 @@ __device__ __forceinline__ typename Num<T>::Pred finite_nonneg(const T (&out)[Q]
     return ok;
 }
 
+// Stability criterion for finite FP32 outputs: ST_UNSTABLE per lane when
+// some f^post_a = W_a rho0 + out_a has its sign bit set.
+template <typename T, int Q>
+__device__ __forceinline__ uint32_t sign_status(const T (&out)[Q], const double (&w)[Q], T rho0) {
+    using N = Num<T>;
+    uint32_t bits[N::LANES];
+#pragma unroll
+    for (int l = 0; l < N::LANES; ++l) bits[l] = 0u;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const T f = N::mad(T((float)w[a]), rho0, out[a]);  // f^post_a, packed
+#pragma unroll
+        for (int l = 0; l < N::LANES; ++l) bits[l] |= __float_as_uint(N::lane(f, l));
+    }
+    uint32_t st = 0;
+#pragma unroll
+    for (int l = 0; l < N::LANES; ++l) st |= (bits[l] >> 31) ? (ST_UNSTABLE << (2 * l)) : 0u;
+    return st;
+}
+
 // 4x4 symmetric positive definite solve A x = b by 2x2 blocks:
 //   A = [P B; B^T C],  P, C 2x2,
 //   Schur complement Z = C - B^T P^-1 B (SPD when A is),
@@ -171,9 +191,13 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
     T y[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) y[a] = T(1.0) + del[a];
-    T mn = N::vmin(N::vmin(N::vmin(y[0], y[1]), N::vmin(y[2], y[3])),
-                   N::vmin(N::vmin(y[4], y[5]), N::vmin(N::vmin(y[6], y[7]), y[8])));
-    const typename N::Pred ok = N::gt(mn, T(0.0));
+    // FP64: the exact test of reading C-NEG.  FP32: see the Newton-step test below.
+    typename N::Pred ok{};
+    if constexpr (std::is_same<T, double>::value) {
+        const T mn = N::vmin(N::vmin(N::vmin(y[0], y[1]), N::vmin(y[2], y[3])),
+                             N::vmin(N::vmin(y[4], y[5]), N::vmin(N::vmin(y[6], y[7]), y[8])));
+        ok = N::gt(mn, T(0.0));
+    }
 
     // ln(p/W) (natural or base-2 logs, see Num::LOG_SCALE) and q_a = W_a / p_a
     T L[9], q[9];
@@ -212,10 +236,33 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
     spd4_solve<T>(A_ee, A_ep, A_pp, A_ex, A_px, A_xx, A_ey, A_py, A_xy, A_yy, b_e, b_p, b_x, b_y,
                   se, sps, sx_, sy_);
     // a node whose start point is not positive keeps p^start (reading C-NEG)
-    se = N::sel(ok, se, T(0.0));
-    sps = N::sel(ok, sps, T(0.0));
-    sx_ = N::sel(ok, sx_, T(0.0));
-    sy_ = N::sel(ok, sy_, T(0.0));
+    bool rare = false;  // some lane skipped its Newton step (FP32 paths)
+    if constexpr (std::is_same<T, double>::value) {
+        se = N::sel(ok, se, T(0.0));
+        sps = N::sel(ok, sps, T(0.0));
+        sx_ = N::sel(ok, sx_, T(0.0));
+        sy_ = N::sel(ok, sy_, T(0.0));
+    } else {
+        // FP32: a start probability <= 0 gives log2 = NaN or -inf, which the
+        // solve carries into every component of the step; a step that is not
+        // finite (this, or an overflowing solve) is skipped.  chk = c - c is
+        // +0 for finite c and NaN otherwise.
+        T chk = (se + sps) + (sx_ + sy_);
+        chk = chk - chk;
+#pragma unroll
+        for (int l = 0; l < N::LANES; ++l) rare = rare || (N::lane(chk, l) != 0.f);
+        if (rare) {
+            if constexpr (N::LANES == 1) {
+                ok = N::lane(chk, 0) == 0.f;
+            } else {
+                ok = {N::lane(chk, 0) == 0.f, N::lane(chk, 1) == 0.f};
+            }
+            se = N::sel(ok, se, T(0.0));
+            sps = N::sel(ok, sps, T(0.0));
+            sx_ = N::sel(ok, sx_, T(0.0));
+            sy_ = N::sel(ok, sy_, T(0.0));
+        }
+    }
     // (T^T s~)_a
     T t[9];
     const T ce = N::mad(T(-2.0), sps, -se);
@@ -238,8 +285,14 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
         const T wa = T(W[a]);
         out[a] = N::mad(-rs, t[a], N::mad(wa * rho, del[a], wa * drho));
     }
-    typename N::Pred notskip = ok;
-    return lane_status<T>(notskip, finite_nonneg<T, 9>(out, W, rho0));
+    if constexpr (std::is_same<T, double>::value) {
+        return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
+    } else {
+        if (rare) return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
+        // every step was finite, and so are the populations: only the sign of
+        // f^post = W rho0 + out remains to test (OR of the sign bits)
+        return sign_status<T, 9>(out, W, rho0);
+    }
 }
 
 // ---------------------------------------------------------------------------
