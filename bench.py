@@ -53,8 +53,10 @@ def parse():
     p.add_argument("--compute", choices=["f32", "f64"], default="f32")
     p.add_argument("--storage", choices=["f16", "bf16", "f32", "f64"], default=None,
                    help="default: the workload's own storage type")
-    p.add_argument("--collision", choices=["minxent4", "srt"], default="minxent4",
-                   help="srt: the SRT-BGK twin kernel (bandwidth reference)")
+    p.add_argument("--collision", choices=["minxent4", "minxent2", "mrt", "trt", "srt"],
+                   default="minxent4",
+                   help="srt: the SRT-BGK twin kernel (bandwidth reference); minxent2, mrt, "
+                        "trt: the paper's other rules")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP64 comparison, e2e and CPU-baseline legs")
     return p.parse_args()
@@ -268,14 +270,17 @@ def traffic_per_node(storage: str):
     return float(e["dram_bytes_per_node"])
 
 
-def _oracle_sim(wk: "Workload", i: int, nx: int | None = None):
+def _oracle_sim(wk: "Workload", i: int, nx: int | None = None, collision: str = "minxent4"):
     """An oracle lattice with instance i's parameters (optionally resized)."""
     import oracle
     from paper_1801_03863_gb300 import workloads as wl
+    coll = {"minxent4": oracle.MINXENT4, "minxent2": oracle.MINXENT2, "mrt": oracle.MRT,
+            "trt": oracle.TRT, "srt": oracle.SRT}[collision]
     nx0, ny0 = wk.dims[i]
     if wk.lattice == "d1q3":
         n = nx or nx0
-        sim = oracle.Sim(oracle.D1Q3, n, 1, oracle.tau_from_nu(wk.nu[i]), oracle.BC_ZERO_GRADIENT)
+        sim = oracle.Sim(oracle.D1Q3, n, 1, oracle.tau_from_nu(wk.nu[i]), oracle.BC_ZERO_GRADIENT,
+                         collision=coll)
         r, x = wl.shock_tube_1d(n)
         sim.init(r, x)
         return sim, n
@@ -286,7 +291,7 @@ def _oracle_sim(wk: "Workload", i: int, nx: int | None = None):
         nu = nu * side / nx0
     ulid = wk.u_lid[i] if wk.u_lid else 0.0
     sim = oracle.Sim(oracle.D2Q9, side, side if nx else ny0, oracle.tau_from_nu(nu), bc,
-                     u_lid=ulid)
+                     collision=coll, u_lid=ulid)
     if wk.bc == "cavity":
         sim.init(*wl.cavity(side, noise=1e-6, seed=0))
     else:
@@ -294,10 +299,10 @@ def _oracle_sim(wk: "Workload", i: int, nx: int | None = None):
     return sim, side * (side if nx else ny0)
 
 
-def cpu_oracle_sample(wk: "Workload", budget_s: float = 12.0):
+def cpu_oracle_sample(wk: "Workload", collision: str, budget_s: float = 12.0):
     """Time the FP64 oracle on instance 0 of the workload for ~budget_s seconds."""
     import oracle
-    sim, nodes = _oracle_sim(wk, 0)
+    sim, nodes = _oracle_sim(wk, 0, collision=collision)
     t0 = time.perf_counter()
     sim.step(2)
     per = (time.perf_counter() - t0) / 2
@@ -309,7 +314,7 @@ def cpu_oracle_sample(wk: "Workload", budget_s: float = 12.0):
     return {"value": lu / dt / 1e9, "unit": "GLUPS", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"instance 0 of the workload ({wk.dims[0][0]}x{wk.dims[0][1]}) x {steps} "
-                      f"steps = {lu / 1e6:.1f} M LU in {dt:.1f} s, FP64 MinxEnt",
+                      f"steps = {lu / 1e6:.1f} M LU in {dt:.1f} s, FP64 {collision.upper()}",
             "host_cpus": os.cpu_count()}
 
 
@@ -324,7 +329,8 @@ def run_reference(args, dist):
     wk = Workload(args.workload, 0, 1)
     # per-step sample: instance 0's parameters on a lattice sized so that the
     # whole --steps/--warmup run takes about two minutes on the host cores
-    probe, pn = _oracle_sim(wk, 0, nx=128 if wk.lattice == "d2q9" else 4096)
+    probe, pn = _oracle_sim(wk, 0, nx=128 if wk.lattice == "d2q9" else 4096,
+                            collision=args.collision)
     t0 = time.perf_counter()
     probe.step(3)
     rate = 3 * pn / (time.perf_counter() - t0)
@@ -334,14 +340,14 @@ def run_reference(args, dist):
         size = int(max(16, min(wk.dims[0][0], math.sqrt(want))))
     else:
         size = int(max(64, min(wk.dims[0][0], want)))
-    sim, nodes = _oracle_sim(wk, 0, nx=size)
+    sim, nodes = _oracle_sim(wk, 0, nx=size, collision=args.collision)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
     dt = time.perf_counter() - t0
     value = nodes * args.steps / dt / 1e9
     sample = (f"instance 0's parameters on {nodes} nodes per step (bounded sample of the "
-              f"{wk.nodes}-node workload), FP64 MinxEnt on {oracle.num_threads()} threads")
+              f"{wk.nodes}-node workload), FP64 {args.collision.upper()} on {oracle.num_threads()} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -458,11 +464,11 @@ def run_ours(args, dist):
     if not args.no_extras and dist.rank == 0:
         line["e2e"] = e2e_leg(args, lat, wk)
         if wk.lattice == "d2q9":
-            line["fp64_plain"] = fp64_plain_leg()
+            line["fp64_plain"] = fp64_plain_leg(args.collision)
         if args.compute == "f32":
             line["error_vs_fp64"] = error_leg(args, wk)
         if dist.world == 1:
-            line["cpu_baseline"] = cpu_oracle_sample(wk)
+            line["cpu_baseline"] = cpu_oracle_sample(wk, args.collision)
     lat.close()
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
@@ -494,11 +500,11 @@ def e2e_leg(args, lat, wk):
             "note": "lbm_init from pinned host arrays + lbm_step(K) + lbm_moments to pinned host"}
 
 
-def fp64_plain_leg(steps: int = 20):
+def fp64_plain_leg(collision: str, steps: int = 20):
     """The plain FP64 single-instance kernel: one 2048^2 cavity, Re 5000, U 0.1."""
     import torch
     wk = Workload("cavity2048", 0, 1)
-    with wk.lattice_obj("f64", "f64") as lat:
+    with wk.lattice_obj("f64", "f64", collision) as lat:
         lat.init(*wk.fields())
         lat.step(3)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -512,7 +518,7 @@ def fp64_plain_leg(steps: int = 20):
         shape = lat.launch_shape()
     peak, _ = measured_peaks()
     glups = wk.nodes / (ms * 1e-3) / 1e9
-    return {"workload": WORKLOADS["cavity2048"] + "; MinxEnt4, FP64 collide and storage",
+    return {"workload": WORKLOADS["cavity2048"] + f"; {collision.upper()}, FP64 collide and storage",
             "value": glups, "unit": "GLUPS", "ms_per_step": ms,
             "hbm_frac": glups * 1e9 * wk.bytes_per_lu("f64") / (peak * 1e9), "launch_shape": shape}
 
@@ -522,7 +528,7 @@ def error_leg(args, wk, steps: int = 100):
     workload after `steps` steps (relative L2 / Linf over all nodes)."""
     res = {}
     for comp, stor in (("f64", "f64"), (args.compute, args.storage)):
-        lat = wk.lattice_obj(comp, stor)
+        lat = wk.lattice_obj(comp, stor, args.collision)
         lat.init(*wk.fields())
         lat.step(steps)
         r, x, y = lat.moments(allow_unstable=True)

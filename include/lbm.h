@@ -71,8 +71,29 @@ typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_ZERO_GRADIENT = 1, LBM_BC_CAVITY = 2 
  *            in moment space from the equilibrium moments.  On D1Q3 the three
  *            constraints fix the populations and the rule equals BGK.
  *  SRT       Eq. (bgkcollision) with the polynomial equilibrium
- *            (Eq. numerical-plyeqm); the bandwidth reference kernel. */
-typedef enum { LBM_MINXENT4 = 0, LBM_SRT = 1 } lbm_collision;
+ *            (Eq. numerical-plyeqm); the bandwidth reference kernel.
+ *  MINXENT2  Sec. IV.C-E with two free moments (M2, M3) and the extra
+ *            heat-flux constraints of Eqs. (extraconstraint1/2), relaxed at
+ *            1/tau2 (Eq. tau2).
+ *  MRT       Eq. (mrtcollision) with Table III's MRT-LBM rates
+ *            diag(0, 1.64, 1.54, 0, 1/tau2, 0, 1/tau2, 1/tau, 1/tau).
+ *  TRT       Eq. (mrtcollision) with Table III's TRT-LBM rates
+ *            diag(0, 1/tau, 1/tau, 0, 1/tau2, 0, 1/tau2, 1/tau, 1/tau).
+ * On D1Q3 every rule relaxes the one non-conserved moment at 1/tau: BGK. */
+typedef enum {
+    LBM_MINXENT4 = 0,
+    LBM_SRT = 1,
+    LBM_MINXENT2 = 2,
+    LBM_MRT = 3,
+    LBM_TRT = 4
+} lbm_collision;
+
+/* Reading of Eq. (tau2) for the heat-flux rate 1/tau2 (MINXENT2, MRT, TRT).
+ *  PRINTED  tau2 = (8 tau - 1) / (2 tau - 1), as printed.
+ *  MAGIC    tau2 = (8 tau - 1) / (8 (2 tau - 1)), the form that gives the
+ *           TRT "magic" product (tau - 1/2)(tau2 - 1/2) = 3/16 of the
+ *           relation the paper cites; the printed form may lack the 8. */
+typedef enum { LBM_TAU2_PRINTED = 0, LBM_TAU2_MAGIC = 1 } lbm_tau2_reading;
 
 /* Arithmetic / storage types.  compute = LBM_F64 requires storage = LBM_F64;
  * compute = LBM_F32 allows storage LBM_F32, LBM_F16 or LBM_BF16. */
@@ -90,6 +111,8 @@ typedef struct {
                                   aligned) of lbm_required_bytes() bytes; NULL = the
                                   library allocates and frees its own                */
     uint64_t device_mem_bytes; /* size of device_mem                                */
+    int32_t tau2_reading;      /* lbm_tau2_reading (default PRINTED)                 */
+    int32_t reserved;          /* must be 0                                         */
 } lbm_opts;
 
 /* Fill *opts with the defaults listed above. */

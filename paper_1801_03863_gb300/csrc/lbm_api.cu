@@ -446,7 +446,9 @@ int validate_opts(const lbm_opts* o) {
     if (o->storage < DT_F64 || o->storage > DT_BF16) return LBM_ERR_ARG;
     if (o->compute == DT_F64 && o->storage != DT_F64) return LBM_ERR_ARG;
     if (o->compute == DT_F32 && o->storage == DT_F64) return LBM_ERR_ARG;
-    if (o->collision != COLL_MINXENT4 && o->collision != COLL_SRT) return LBM_ERR_ARG;
+    if (o->collision < COLL_MINXENT4 || o->collision > COLL_TRT) return LBM_ERR_ARG;
+    if (o->tau2_reading != TAU2_PRINTED && o->tau2_reading != TAU2_MAGIC) return LBM_ERR_ARG;
+    if (o->reserved != 0) return LBM_ERR_ARG;
     if (!(o->rho0 > 0.0) || !std::isfinite(o->rho0)) return LBM_ERR_ARG;
     return LBM_OK;
 }
@@ -555,6 +557,13 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
         const double tau = 3.0 * nu[i] + 0.5;
         in.bc = bc;
         in.omega = 1.0 / tau;
+        // Eq. (tau2), as printed or in the magic-parameter reading
+        const double tau2 = (8.0 * tau - 1.0) /
+                            ((o.tau2_reading == TAU2_MAGIC ? 8.0 : 1.0) * (2.0 * tau - 1.0));
+        in.omega2 = 1.0 / tau2;
+        // Table III: MRT fixes the energy rates, TRT uses 1/tau for them
+        in.s_e = o.collision == COLL_MRT ? 1.64 : in.omega;
+        in.s_eps = o.collision == COLL_MRT ? 1.54 : in.omega;
         in.u_lid = u_lid ? u_lid[i] : 0.0;
         if (bc == LBM_BC_CAVITY) {
             lid_deviation(o.rho0, in.u_lid, in.lid_dev);

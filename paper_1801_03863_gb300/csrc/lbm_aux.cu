@@ -105,7 +105,8 @@ __global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* ins
             if constexpr (std::is_same<T, double>::value) d[a] = Store<S>::to_f64(v);
             else d[a] = CT(Store<S>::to_f32(v));
         }
-        uint32_t st = Collide<Lat, COLL, CT>::run(d, CT((T)rho0), CT((T)in.omega), o);
+        const Rates<CT> rates{CT((T)in.omega), CT((T)in.omega2), CT((T)in.s_e), CT((T)in.s_eps)};
+        uint32_t st = Collide<Lat, COLL, CT>::run(d, CT((T)rho0), rates, o);
         if (in.bc == BC_CAVITY) {
             const bool wall = (x == 0) || (x == in.nx - 1) || (y == 0);
             const bool lid = !wall && (y == in.ny - 1);
@@ -204,10 +205,10 @@ __device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, 
 // Conservation, pass 1: block b of instance i sums (sum d, sum d v_x,
 // sum d v_y) over nodes k = b*256 + t + j*P*256 and reduces the block in a
 // fixed tree; partials[(i*P + b)*3 + c].  The grid (P blocks per instance)
-// is a constant, so the summation order is fixed.  The node-level sums of
-// 2- and 4-byte storage run in FP32 (nine deviations of that precision; the
-// rounding of these small sums is far below the stored values' own), every
-// sum across nodes runs in FP64.
+// is a constant, so the summation order is fixed.  Every sum runs in FP64,
+// except the node-level sums of 2-byte storage, which add the nine 11- or
+// 8-bit-significand deviations in FP32 (error below 9 * 2^-24 * sum |d|, far
+// under the storage rounding itself) before the FP64 sums across nodes.
 template <class Lat, typename S>
 __global__ void __launch_bounds__(AUX_THREADS)
 cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* partials) {
@@ -218,14 +219,14 @@ cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* pa
     for (int64_t k = (int64_t)blockIdx.x * AUX_THREADS + threadIdx.x; k < n;
          k += (int64_t)CONS_PARTIALS * AUX_THREADS) {
         const int x = (int)(k % in.nx), y = (int)(k / in.nx);
-        if constexpr (std::is_same<S, double>::value) {
+        if constexpr (sizeof(S) >= 4) {
             double d[Lat::Q];
             node_state<Lat, S>(src, in, x, y, pulled, d);
 #pragma unroll
             for (int a = 0; a < Lat::Q; ++a) {
                 s0 += d[a];
-                s1 += Lat::vx(a) * d[a];
-                s2 += Lat::vy(a) * d[a];
+                if (Lat::vx(a) != 0) s1 += Lat::vx(a) * d[a];
+                if (Lat::vy(a) != 0) s2 += Lat::vy(a) * d[a];
             }
         } else {
             float d[Lat::Q];
@@ -287,6 +288,23 @@ cudaError_t collide_inplace_dispatch(const AuxArgs& a, const void* src, void* ds
     return cudaGetLastError();
 }
 
+// TRT shares the MRT kernel; on D1Q3 every rule is BGK.
+template <class Lat, typename S, typename T>
+cudaError_t collide_inplace_by_rule(const AuxArgs& a, const void* src, void* dst) {
+    if constexpr (Lat::Q == 3) {
+        return collide_inplace_dispatch<Lat, S, T, COLL_MINXENT4>(a, src, dst);
+    } else {
+        switch (a.collision) {
+            case COLL_MINXENT4: return collide_inplace_dispatch<Lat, S, T, COLL_MINXENT4>(a, src, dst);
+            case COLL_SRT: return collide_inplace_dispatch<Lat, S, T, COLL_SRT>(a, src, dst);
+            case COLL_MINXENT2: return collide_inplace_dispatch<Lat, S, T, COLL_MINXENT2>(a, src, dst);
+            case COLL_MRT:
+            case COLL_TRT: return collide_inplace_dispatch<Lat, S, T, COLL_MRT>(a, src, dst);
+        }
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <class Lat, typename S>
 cudaError_t aux_dispatch(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
                          const double* p1, const double* p2, double* o0, double* o1, double* o2) {
@@ -317,16 +335,11 @@ cudaError_t aux_dispatch(AuxOp op, const AuxArgs& a, const void* src, void* dst,
         }
         case AuxOp::CollideInPlace: {
             if (a.compute == DT_F64) {
-                if constexpr (std::is_same<S, double>::value) {
-                    return a.collision == COLL_SRT
-                               ? collide_inplace_dispatch<Lat, S, double, COLL_SRT>(a, src, dst)
-                               : collide_inplace_dispatch<Lat, S, double, COLL_MINXENT4>(a, src, dst);
-                }
+                if constexpr (std::is_same<S, double>::value)
+                    return collide_inplace_by_rule<Lat, S, double>(a, src, dst);
                 return cudaErrorInvalidValue;
             }
-            return a.collision == COLL_SRT
-                       ? collide_inplace_dispatch<Lat, S, float, COLL_SRT>(a, src, dst)
-                       : collide_inplace_dispatch<Lat, S, float, COLL_MINXENT4>(a, src, dst);
+            return collide_inplace_by_rule<Lat, S, float>(a, src, dst);
         }
     }
     return cudaGetLastError();

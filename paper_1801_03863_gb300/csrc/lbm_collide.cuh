@@ -27,6 +27,17 @@
 //     s8 = P_xx/rho - (u_x^2 - u_y^2),  s9 = P_xy/rho - u_x u_y,
 // so ln(p_a/W_a) = ln(1 + delta_a) is formed without cancellation.
 //
+// MinxEnt2 (same sections) frees only the energy moments m = (M2, M3) and
+// adds the heat-flux constraints c5, c7 (Eqs. extraconstraint1/2): M5 and M7
+// relax at rate 1/tau2 (Eq. tau2).  Its start point adds to delta_a the
+// relaxed heat-flux term
+//     (T_5a g_x + T_7a g_y) / (12 W_a),  g = (1 - omega2)(q^pre - q^eq)/rho,
+// and the Newton system shrinks to the 2x2 block of A for (M2, M3).
+//
+// MRT and TRT (Eq. mrtcollision with the diagonal rates of Table III) relax
+// each non-conserved moment k of f toward f^eq at its own rate B_k:
+//     f^post_a = f_a + sum_k T_ka B_k (m^eq_k - m_k) / d_k.
+//
 // The rules are templates over the number type T of lbm_num.cuh (double,
 // float, or F2 = two nodes at once); a[b] below always means a * b + c with
 // one rounding (Num<T>::mad).
@@ -35,6 +46,14 @@
 #include "lbm_num.cuh"
 
 namespace lbm {
+
+// Relaxation rates of one instance, in the collision's number type.
+template <typename T> struct Rates {
+    T omega;   // 1 / tau     (M8, M9; SRT: every moment)
+    T omega2;  // 1 / tau2    (M5, M7: MinxEnt2, MRT, TRT)
+    T s_e;     // M2 rate     (MRT, TRT)
+    T s_eps;   // M3 rate     (MRT, TRT)
+};
 
 // Status bits of lane l are (ST_* << 2 l).
 template <typename T>
@@ -139,17 +158,21 @@ __device__ __forceinline__ void spd4_solve(T a11, T a21, T a22, T a31, T a32, T 
 }
 
 // ---------------------------------------------------------------------------
-// D2Q9 MinxEnt4 collision of one fluid node (or two, T = F2).
+// D2Q9 MinxEnt collision of one fluid node (or two, T = F2).
+//   NFREE  4 (MinxEnt4: free M2, M3, M5, M7) or 2 (MinxEnt2: free M2, M3)
 //   d      pulled pre-collision deviations f_a - W_a rho0
-//   rho0   reference density; omega = 1/tau
+//   rho0   reference density; r.omega = 1/tau, r.omega2 = 1/tau2
 //   out    post-collision deviations
 // Returns ST_* bits per lane: ST_NEWTON_SKIPPED when some p^start_a <= 0
 // (the node keeps p^start, which meets every constraint), ST_UNSTABLE when
 // some post-collision population is negative or not finite.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T omega, T (&out)[9]) {
+template <typename T, int NFREE>
+__device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const Rates<T>& r,
+                                                 T (&out)[9]) {
+    static_assert(NFREE == 4 || NFREE == 2, "MinxEnt4 or MinxEnt2");
     using N = Num<T>;
+    const T omega = r.omega;
     constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
     // Moments of the pulled state (Sec. II.A) and the stress moments
@@ -177,15 +200,30 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
     const T sp = N::mad(T(4.5) * sp_, sp_, b0 + c9);
     const T sm = N::mad(T(4.5) * dm_, dm_, b0 - c9);
     T del[9];
+    // coefficients of the terms odd in v: 3 v.u, plus for MinxEnt2 the
+    // relaxed heat flux, T_5a g_x / (12 W_a) = (-3/2 on +x, +3 on (+,+) ...)
+    T hx = ux, hy = uy, lp = sp_, lm = dm_;
+    if constexpr (NFREE == 2) {
+        // q^pre - q^eq = -Q with Q_x = (d1 - d3) - 2 (a57 + a86) (deviation
+        // form of m^eq_5 - m_5 = -rho u_x - M5), likewise Q_y
+        const T Qx = N::mad(T(-2.0), a57 + a86, d[1] - d[3]);
+        const T Qy = N::mad(T(-2.0), a57 - a86, d[2] - d[4]);
+        const T k2 = (r.omega2 - T(1.0)) * ir;  // g = (omega2 - 1) Q / rho
+        const T gx = k2 * Qx, gy = k2 * Qy;
+        hx = N::mad(T(-0.5), gx, ux);
+        hy = N::mad(T(-0.5), gy, uy);
+        lp = sp_ + (gx + gy);
+        lm = dm_ + (gy - gx);
+    }
     del[0] = b0;
-    del[1] = N::mad(T(3.0), ux, sx);
-    del[3] = N::mad(T(-3.0), ux, sx);
-    del[2] = N::mad(T(3.0), uy, sy);
-    del[4] = N::mad(T(-3.0), uy, sy);
-    del[5] = N::mad(T(3.0), sp_, sp);
-    del[7] = N::mad(T(-3.0), sp_, sp);
-    del[6] = N::mad(T(3.0), dm_, sm);
-    del[8] = N::mad(T(-3.0), dm_, sm);
+    del[1] = N::mad(T(3.0), hx, sx);
+    del[3] = N::mad(T(-3.0), hx, sx);
+    del[2] = N::mad(T(3.0), hy, sy);
+    del[4] = N::mad(T(-3.0), hy, sy);
+    del[5] = N::mad(T(3.0), lp, sp);
+    del[7] = N::mad(T(-3.0), lp, sp);
+    del[6] = N::mad(T(3.0), lm, sm);
+    del[8] = N::mad(T(-3.0), lm, sm);
 
     // y_a = p^start_a / W_a; all positive <=> the logarithms exist (reading C-NEG)
     T y[9];
@@ -218,36 +256,45 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
     const T A_ee = N::mad(T(16.0), qd, N::mad(T(4.0), q[0], Qa));
     const T A_ep = N::mad(T(8.0), qd, N::mad(T(-4.0), q[0], Qa + Qa));
     const T A_pp = T(4.0) * (q[0] + Qa + qd);
-    const T A_ex = N::mad(T(8.0), dx, d13 + d13);
-    const T A_px = T(4.0) * (d13 + dx);
-    const T A_xx = T(4.0) * (p13 + qd);
-    const T A_ey = N::mad(T(8.0), dy, d24 + d24);
-    const T A_py = T(4.0) * (d24 + dy);
-    const T A_yy = T(4.0) * (p24 + qd);
-    const T A_xy = T(4.0) * (s57 - s68);
     const T La = (L[1] + L[2]) + (L[3] + L[4]);
     const T Ld = (L[5] + L[6]) + (L[7] + L[8]);
-    const T l57 = L[5] - L[7], l68 = L[6] - L[8];
     const T b_e = N::mad(T(-4.0), L[0], N::mad(T(2.0), Ld, -La));
     const T b_p = N::mad(T(4.0), L[0], N::mad(T(-2.0), La, Ld));
-    const T b_x = N::mad(T(2.0), L[3] - L[1], l57 - l68);
-    const T b_y = N::mad(T(2.0), L[4] - L[2], l57 + l68);
-    T se, sps, sx_, sy_;
-    spd4_solve<T>(A_ee, A_ep, A_pp, A_ex, A_px, A_xx, A_ey, A_py, A_xy, A_yy, b_e, b_p, b_x, b_y,
-                  se, sps, sx_, sy_);
+    T se, sps, sx_ = T(0.0), sy_ = T(0.0);
+    if constexpr (NFREE == 4) {
+        const T A_ex = N::mad(T(8.0), dx, d13 + d13);
+        const T A_px = T(4.0) * (d13 + dx);
+        const T A_xx = T(4.0) * (p13 + qd);
+        const T A_ey = N::mad(T(8.0), dy, d24 + d24);
+        const T A_py = T(4.0) * (d24 + dy);
+        const T A_yy = T(4.0) * (p24 + qd);
+        const T A_xy = T(4.0) * (s57 - s68);
+        const T l57 = L[5] - L[7], l68 = L[6] - L[8];
+        const T b_x = N::mad(T(2.0), L[3] - L[1], l57 - l68);
+        const T b_y = N::mad(T(2.0), L[4] - L[2], l57 + l68);
+        spd4_solve<T>(A_ee, A_ep, A_pp, A_ex, A_px, A_xx, A_ey, A_py, A_xy, A_yy, b_e, b_p, b_x,
+                      b_y, se, sps, sx_, sy_);
+    } else {
+        // 2x2 SPD solve by Cramer's rule
+        const T idet = N::rcp(N::mad(A_ee, A_pp, -(A_ep * A_ep)));
+        se = N::mad(A_pp, b_e, -(A_ep * b_p)) * idet;
+        sps = N::mad(A_ee, b_p, -(A_ep * b_e)) * idet;
+    }
     // a node whose start point is not positive keeps p^start (reading C-NEG)
     bool rare = false;  // some lane skipped its Newton step (FP32 paths)
     if constexpr (std::is_same<T, double>::value) {
         se = N::sel(ok, se, T(0.0));
         sps = N::sel(ok, sps, T(0.0));
-        sx_ = N::sel(ok, sx_, T(0.0));
-        sy_ = N::sel(ok, sy_, T(0.0));
+        if constexpr (NFREE == 4) {
+            sx_ = N::sel(ok, sx_, T(0.0));
+            sy_ = N::sel(ok, sy_, T(0.0));
+        }
     } else {
         // FP32: a start probability <= 0 gives log2 = NaN or -inf, which the
         // solve carries into every component of the step; a step that is not
         // finite (this, or an overflowing solve) is skipped.  chk = c - c is
         // +0 for finite c and NaN otherwise.
-        T chk = (se + sps) + (sx_ + sy_);
+        T chk = (NFREE == 4) ? (se + sps) + (sx_ + sy_) : se + sps;
         chk = chk - chk;
 #pragma unroll
         for (int l = 0; l < N::LANES; ++l) rare = rare || (N::lane(chk, l) != 0.f);
@@ -259,24 +306,31 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
             }
             se = N::sel(ok, se, T(0.0));
             sps = N::sel(ok, sps, T(0.0));
-            sx_ = N::sel(ok, sx_, T(0.0));
-            sy_ = N::sel(ok, sy_, T(0.0));
+            if constexpr (NFREE == 4) {
+                sx_ = N::sel(ok, sx_, T(0.0));
+                sy_ = N::sel(ok, sy_, T(0.0));
+            }
         }
     }
     // (T^T s~)_a
     T t[9];
     const T ce = N::mad(T(-2.0), sps, -se);
     const T cd = N::mad(T(2.0), se, sps);
-    const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
     t[0] = T(4.0) * (sps - se);
-    t[1] = N::mad(T(-2.0), sx_, ce);
-    t[3] = N::mad(T(2.0), sx_, ce);
-    t[2] = N::mad(T(-2.0), sy_, ce);
-    t[4] = N::mad(T(2.0), sy_, ce);
-    t[5] = cd + pxy_;
-    t[7] = cd - pxy_;
-    t[6] = cd - mxy_;
-    t[8] = cd + mxy_;
+    if constexpr (NFREE == 4) {
+        const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
+        t[1] = N::mad(T(-2.0), sx_, ce);
+        t[3] = N::mad(T(2.0), sx_, ce);
+        t[2] = N::mad(T(-2.0), sy_, ce);
+        t[4] = N::mad(T(2.0), sy_, ce);
+        t[5] = cd + pxy_;
+        t[7] = cd - pxy_;
+        t[6] = cd - mxy_;
+        t[8] = cd + mxy_;
+    } else {
+        t[1] = t[2] = t[3] = t[4] = ce;
+        t[5] = t[6] = t[7] = t[8] = cd;
+    }
     // d^post_a = W_a (drho + rho delta_a) - rho (T^T s~)_a; the 1/9 of A's
     // scaling and the log base go into the last factor.
     const T rs = rho * T(N::LOG_SCALE / 9.0);
@@ -299,8 +353,10 @@ __device__ __forceinline__ uint32_t minxent4_d2q9(const T (&d)[9], T rho0, T ome
 // D2Q9 SRT/BGK collision, Eq. (bgkcollision): f + omega (f^eq - f).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ uint32_t srt_d2q9(const T (&d)[9], T rho0, T omega, T (&out)[9]) {
+__device__ __forceinline__ uint32_t srt_d2q9(const T (&d)[9], T rho0, const Rates<T>& r,
+                                             T (&out)[9]) {
     using N = Num<T>;
+    const T omega = r.omega;
     constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
     const T drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
@@ -338,13 +394,79 @@ __device__ __forceinline__ uint32_t srt_d2q9(const T (&d)[9], T rho0, T omega, T
 }
 
 // ---------------------------------------------------------------------------
+// D2Q9 MRT / TRT collision, Eq. (mrtcollision): the moments of T relax
+// toward those of the polynomial equilibrium at the rates of Table III,
+//   B = diag(0, s_e, s_eps, 0, omega2, 0, omega2, omega, omega),
+// MRT: s_e = 1.64, s_eps = 1.54; TRT: s_e = s_eps = omega.  In deviation
+// variables (m_k(W) = (1, -2, 1, 0, ...)) the moment differences are
+//   m^eq_2 - m_2 = 2 d0 - S_a - 4 S_d + 3 rho u^2,
+//   m^eq_3 - m_3 = 3 (S_a - d0 - rho u^2),
+//   m^eq_5 - m_5 = (d1 - d3) - 2 (a57 + a86),  m^eq_7 - m_7 likewise,
+//   m^eq_8 - m_8 = rho (u_x^2 - u_y^2) - P_xx,  m^eq_9 - m_9 = rho u_x u_y - P_xy,
+// with S_a, S_d the axis and diagonal sums; each is scaled by B_k / d_k and
+// mapped back with the columns of T.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ uint32_t mrt_d2q9(const T (&d)[9], T rho0, const Rates<T>& r,
+                                             T (&out)[9]) {
+    using N = Num<T>;
+    constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    const T Sa = (d[1] + d[2]) + (d[3] + d[4]);
+    const T Sd = (d[5] + d[6]) + (d[7] + d[8]);
+    const T drho = d[0] + Sa + Sd;
+    const T a57 = d[5] - d[7], a86 = d[8] - d[6];
+    const T d13 = d[1] - d[3], d24 = d[2] - d[4];
+    const T jx = d13 + a57 + a86;
+    const T jy = d24 + a57 - a86;
+    const T pxx = (d[1] + d[3]) - (d[2] + d[4]);
+    const T pxy = (d[5] + d[7]) - (d[6] + d[8]);
+    const T rho = rho0 + drho;
+    const T ir = N::rcp(rho);
+    const T ux = jx * ir, uy = jy * ir;
+    const T ru2 = N::mad(jx, ux, jy * uy);  // rho u^2
+    const T Ee = N::mad(T(3.0), ru2, N::mad(T(2.0), d[0], N::mad(T(-4.0), Sd, -Sa)));
+    const T Ep = T(3.0) * ((Sa - d[0]) - ru2);
+    const T Qx = N::mad(T(-2.0), a57 + a86, d13);
+    const T Qy = N::mad(T(-2.0), a57 - a86, d24);
+    const T P8 = N::mad(jx, ux, -N::mad(jy, uy, pxx));
+    const T P9 = N::mad(jx, uy, -pxy);
+    const T re = (r.s_e * T(1.0 / 36.0)) * Ee;
+    const T rp = (r.s_eps * T(1.0 / 36.0)) * Ep;
+    const T rx = (r.omega2 * T(1.0 / 12.0)) * Qx;
+    const T ry = (r.omega2 * T(1.0 / 12.0)) * Qy;
+    const T r8 = (r.omega * T(0.25)) * P8;
+    const T r9 = (r.omega * T(0.25)) * P9;
+    const T c = N::mad(T(-2.0), rp, -re);  // axis columns of rows 2, 3
+    const T g = N::mad(T(2.0), re, rp);    // diagonal columns of rows 2, 3
+    const T cp = c + r8, cm = c - r8;
+    const T xp = rx + ry, xm = rx - ry;
+    const T gp = g + r9, gm = g - r9;
+    out[0] = N::mad(T(4.0), rp - re, d[0]);
+    out[1] = d[1] + N::mad(T(-2.0), rx, cp);
+    out[3] = d[3] + N::mad(T(2.0), rx, cp);
+    out[2] = d[2] + N::mad(T(-2.0), ry, cm);
+    out[4] = d[4] + N::mad(T(2.0), ry, cm);
+    out[5] = d[5] + (gp + xp);
+    out[7] = d[7] + (gp - xp);
+    out[6] = d[6] + (gm - xm);
+    out[8] = d[8] + (gm + xm);
+    typename N::Pred all;
+    if constexpr (N::LANES == 1) all = true;
+    else all = {true, true};
+    return lane_status<T>(all, finite_nonneg<T, 9>(out, W, rho0));
+}
+
+// ---------------------------------------------------------------------------
 // D1Q3 collision.  MinxEnt on D1Q3: mass, momentum and the relaxed second
 // moment fix all three populations, and BGK relaxation meets the same three
 // constraints, so both rules reduce to f + omega (f^eq - f).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, T omega, T (&out)[3]) {
+__device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, const Rates<T>& r,
+                                             T (&out)[3]) {
     using N = Num<T>;
+    const T omega = r.omega;
     constexpr double W[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
     const T drho = d[0] + d[1] + d[2];
     const T rho = rho0 + drho;
@@ -367,18 +489,34 @@ __device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, T omega, T
 // Dispatch by lattice and rule.
 template <class Lat, int COLL, typename T> struct Collide;
 template <typename T> struct Collide<D2Q9, COLL_MINXENT4, T> {
-    __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, T omega, T (&o)[9]) {
-        return minxent4_d2q9<T>(d, rho0, omega, o);
+    __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
+                                                   T (&o)[9]) {
+        return minxent_d2q9<T, 4>(d, rho0, r, o);
+    }
+};
+template <typename T> struct Collide<D2Q9, COLL_MINXENT2, T> {
+    __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
+                                                   T (&o)[9]) {
+        return minxent_d2q9<T, 2>(d, rho0, r, o);
     }
 };
 template <typename T> struct Collide<D2Q9, COLL_SRT, T> {
-    __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, T omega, T (&o)[9]) {
-        return srt_d2q9<T>(d, rho0, omega, o);
+    __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
+                                                   T (&o)[9]) {
+        return srt_d2q9<T>(d, rho0, r, o);
     }
 };
+template <typename T> struct Collide<D2Q9, COLL_MRT, T> {
+    __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
+                                                   T (&o)[9]) {
+        return mrt_d2q9<T>(d, rho0, r, o);
+    }
+};
+// D1Q3: every rule reduces to BGK (one non-conserved moment, relaxed at 1/tau)
 template <int C, typename T> struct Collide<D1Q3, C, T> {
-    __device__ static __forceinline__ uint32_t run(const T (&d)[3], T rho0, T omega, T (&o)[3]) {
-        return bgk_d1q3<T>(d, rho0, omega, o);
+    __device__ static __forceinline__ uint32_t run(const T (&d)[3], T rho0, const Rates<T>& r,
+                                                   T (&o)[3]) {
+        return bgk_d1q3<T>(d, rho0, r, o);
     }
 };
 

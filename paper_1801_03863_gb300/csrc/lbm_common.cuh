@@ -46,9 +46,11 @@ static_assert(D2Q9::opp(1) == 3 && D2Q9::opp(2) == 4 && D2Q9::opp(3) == 1 && D2Q
 static_assert(D2Q9::opp(5) == 7 && D2Q9::opp(6) == 8 && D2Q9::opp(7) == 5 && D2Q9::opp(8) == 6,
               "diagonal opposites");
 
-// Boundary and collision codes (values of the public enums).
+// Boundary and collision codes (values of the public enums).  TRT runs on
+// the MRT kernel with its own rates, so the kernels know four rules.
 enum : int { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_CAVITY = 2 };
-enum : int { COLL_MINXENT4 = 0, COLL_SRT = 1 };
+enum : int { COLL_MINXENT4 = 0, COLL_SRT = 1, COLL_MINXENT2 = 2, COLL_MRT = 3, COLL_TRT = 4 };
+enum : int { TAU2_PRINTED = 0, TAU2_MAGIC = 1 };
 enum : int { DT_F64 = 0, DT_F32 = 1, DT_F16 = 2, DT_BF16 = 3 };
 
 // Status bits of one node.
@@ -91,7 +93,9 @@ struct InstDesc {
     int64_t plane;      // elements per population plane (pitch * ny)
     int64_t node0;      // index of this instance's first node in concatenated host arrays
     int32_t nx, ny, pitch, bc;
-    double omega;       // 1 / tau
+    double omega;       // 1 / tau: rate of the stress moments (M8, M9)
+    double omega2;      // 1 / tau2: rate of the heat-flux moments (M5, M7; MinxEnt2, MRT, TRT)
+    double s_e, s_eps;  // rates of the energy moments M2, M3 (MRT, TRT)
     double u_lid;       // lid speed (cavity only)
     double lid_dev[9];  // f^eq_a(rho0, (u_lid, 0)) - W_a rho0, FP64
     float lid_dev_f[9]; // the same rounded to FP32

@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
             T>::type;
         using N = Num<CT>;
         constexpr int P = N::LANES;
-        const CT omega = CT((typename LaneOf<CT>::type)in.omega);
-        const CT rho0v = CT((typename LaneOf<CT>::type)rho0);
+        using LT = typename LaneOf<CT>::type;
+        const Rates<CT> rates{CT((LT)in.omega), CT((LT)in.omega2), CT((LT)in.s_e), CT((LT)in.s_eps)};
+        const CT rho0v = CT((LT)rho0);
         const bool cavity_edge =
             (bc == BC_CAVITY) && (y == 0 || y == ny - 1 || x0 == 0 || x0 + V >= nx);
         Chunk<S, V> out[Q];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
                     else N::set_lane(d[a], l, to_compute<float, S>(s));
                 }
             }
-            uint32_t st = Collide<Lat, COLL, CT>::run(d, rho0v, omega, o);
+            uint32_t st = Collide<Lat, COLL, CT>::run(d, rho0v, rates, o);
             if (cavity_edge) {
 #pragma unroll
                 for (int l = 0; l < P; ++l) {
@@ -308,6 +309,22 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
         }
         }  // active
     }
+}
+
+// The __global__ function for (lattice, collision rule) with storage S,
+// arithmetic T and V nodes per thread.  TRT shares the MRT kernel (its rates
+// come from the instance table); on D1Q3 every rule is BGK.
+template <typename S, typename T, int V>
+const void* pick_step_kernel(int lattice, int collision) {
+    if (lattice == 1) return (const void*)&step_kernel<D1Q3, S, T, V, COLL_MINXENT4>;
+    switch (collision) {
+        case COLL_MINXENT4: return (const void*)&step_kernel<D2Q9, S, T, V, COLL_MINXENT4>;
+        case COLL_SRT: return (const void*)&step_kernel<D2Q9, S, T, V, COLL_SRT>;
+        case COLL_MINXENT2: return (const void*)&step_kernel<D2Q9, S, T, V, COLL_MINXENT2>;
+        case COLL_MRT:
+        case COLL_TRT: return (const void*)&step_kernel<D2Q9, S, T, V, COLL_MRT>;
+    }
+    return nullptr;
 }
 
 }  // namespace lbm

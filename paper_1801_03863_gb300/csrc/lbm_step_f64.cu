@@ -5,13 +5,7 @@
 namespace lbm {
 
 const void* step_kernel_f64(int lattice, int collision, int V) {
-    if (V == 2) {
-        if (lattice == 2)
-            return collision == COLL_SRT
-                       ? (const void*)&step_kernel<D2Q9, double, double, 2, COLL_SRT>
-                       : (const void*)&step_kernel<D2Q9, double, double, 2, COLL_MINXENT4>;
-        return (const void*)&step_kernel<D1Q3, double, double, 2, COLL_MINXENT4>;
-    }
+    if (V == 2) return pick_step_kernel<double, double, 2>(lattice, collision);
     return nullptr;
 }
 

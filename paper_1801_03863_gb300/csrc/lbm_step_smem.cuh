@@ -65,7 +65,7 @@ struct SmemTile {
 struct StageParams {
     int64_t off, pitch, plane;
     int32_t inst, X, x0, y0, nx, ny, bc, R;
-    float omega;
+    float omega, omega2, s_e, s_eps;
     float lid[9];
 };
 static_assert(sizeof(StageParams) <= 128, "stage parameters must fit 128 bytes");
@@ -279,6 +279,9 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
         p.inst = tile.inst; p.X = tile.pad; p.x0 = tile.cx0; p.y0 = tile.y0;
         p.nx = in.nx; p.ny = in.ny; p.bc = in.bc; p.R = TS::TILE_NODES / tile.pad;
         p.omega = (float)in.omega;
+        p.omega2 = (float)in.omega2;
+        p.s_e = (float)in.s_e;
+        p.s_eps = (float)in.s_eps;
 #pragma unroll
         for (int a = 0; a < Q; ++a) p.lid[a] = in.lid_dev_f[a];
         const uint32_t bytes = (uint32_t)(Q * p.R * (p.X + 2 * E) * sizeof(S));
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
         // own position in a shared row: element E + P px (in words for pairs
         // of 2-byte types)
         const int wb = (P == 1) ? (E + px) : ((sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px));
-        const CT omega = CT(p.omega);
+        const Rates<CT> rates{CT(p.omega), CT(p.omega2), CT(p.s_e), CT(p.s_eps)};
         uint32_t n_skip = 0, n_unst = 0;
         const bool second = (P == 2) && (x + 1 < nx);
         const bool xedge = (x == 0) || (x + P - 1 >= nx - 1);
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                 }
             }
             CT o[Q];
-            uint32_t sts = Collide<D2Q9, COLL, CT>::run(d, rho0v, omega, o);
+            uint32_t sts = Collide<D2Q9, COLL, CT>::run(d, rho0v, rates, o);
             if (bc == BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
 #pragma unroll
                 for (int l = 0; l < P; ++l) {
@@ -423,6 +426,24 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                 mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1));
         }
     }
+}
+
+// The TMA-staged D2Q9 kernel for a collision rule, P nodes per unit, with
+// the default tile geometry of storage S; *smem_bytes receives its dynamic
+// shared memory size.
+template <typename S, int P>
+const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
+    using TS = SmemTile<S>;
+    *smem_bytes = TS::SMEM_BYTES;
+    constexpr int TN = TS::TILE_NODES, NS = TS::STAGES;
+    switch (collision) {
+        case COLL_MINXENT4: return (const void*)&step_kernel_smem<S, COLL_MINXENT4, TN, NS, P>;
+        case COLL_SRT: return (const void*)&step_kernel_smem<S, COLL_SRT, TN, NS, P>;
+        case COLL_MINXENT2: return (const void*)&step_kernel_smem<S, COLL_MINXENT2, TN, NS, P>;
+        case COLL_MRT:
+        case COLL_TRT: return (const void*)&step_kernel_smem<S, COLL_MRT, TN, NS, P>;
+    }
+    return nullptr;
 }
 
 }  // namespace lbm

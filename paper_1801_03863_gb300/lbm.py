@@ -21,11 +21,14 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_ALLOC, LBM_ERR_CUDA = 0, -1, -2, -3
 LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NODEV, LBM_ERR_TIMEOUT = -4, -5, -6, -7
 LBM_D1Q3, LBM_D2Q9 = 1, 2
 LBM_BC_PERIODIC, LBM_BC_ZERO_GRADIENT, LBM_BC_CAVITY = 0, 1, 2
-LBM_MINXENT4, LBM_SRT = 0, 1
+LBM_MINXENT4, LBM_SRT, LBM_MINXENT2, LBM_MRT, LBM_TRT = 0, 1, 2, 3, 4
+LBM_TAU2_PRINTED, LBM_TAU2_MAGIC = 0, 1
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 
 DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
-COLLISIONS = {"minxent4": LBM_MINXENT4, "srt": LBM_SRT}
+COLLISIONS = {"minxent4": LBM_MINXENT4, "srt": LBM_SRT, "minxent2": LBM_MINXENT2, "mrt": LBM_MRT,
+              "trt": LBM_TRT}
+TAU2_READINGS = {"printed": LBM_TAU2_PRINTED, "magic": LBM_TAU2_MAGIC}
 BCS = {"periodic": LBM_BC_PERIODIC, "zero_gradient": LBM_BC_ZERO_GRADIENT, "cavity": LBM_BC_CAVITY}
 
 # Every symbol the header declares (checked by the ABI test).
@@ -49,6 +52,8 @@ class lbm_opts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("device_mem", ctypes.c_void_p),
         ("device_mem_bytes", ctypes.c_uint64),
+        ("tau2_reading", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -249,7 +254,8 @@ class Lattice:
 
     def __init__(self, lattice: str, dims, nu, bc: str, u_lid=None, compute: str = "f64",
                  storage: str | None = None, collision: str = "minxent4", rho0: float = 1.0,
-                 autotune: bool = True, stream=None, torch_memory: bool = True):
+                 autotune: bool = True, stream=None, torch_memory: bool = True,
+                 tau2_reading: str = "printed"):
         import torch
 
         if not torch.cuda.is_available():
@@ -269,6 +275,7 @@ class Lattice:
         o.compute = DTYPES[compute]
         o.storage = DTYPES[storage]
         o.collision = COLLISIONS[collision]
+        o.tau2_reading = TAU2_READINGS[tau2_reading]
         o.autotune = int(bool(autotune))
         o.rho0 = float(rho0)
         self.stream = stream if stream is not None else torch.cuda.Stream()

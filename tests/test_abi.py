@@ -110,3 +110,51 @@ def test_create_without_device_reports_nodev(lib):
     except ImportError:
         pass
     assert _create_code(lib, 2, [16, 16], 1e-3, 0) == lbm.LBM_ERR_NODEV
+
+
+def _header_enum(name):
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", src).group(1)
+    return {k: int(v) for k, v in re.findall(r"(LBM_[A-Z0-9_]+)\s*=\s*(-?\d+)", body)}
+
+
+def test_enums_match_header(lib):
+    coll = _header_enum("lbm_collision")
+    assert coll == {"LBM_MINXENT4": lbm.LBM_MINXENT4, "LBM_SRT": lbm.LBM_SRT,
+                    "LBM_MINXENT2": lbm.LBM_MINXENT2, "LBM_MRT": lbm.LBM_MRT,
+                    "LBM_TRT": lbm.LBM_TRT}
+    assert set(lbm.COLLISIONS.values()) == set(coll.values())
+    t2 = _header_enum("lbm_tau2_reading")
+    assert t2 == {"LBM_TAU2_PRINTED": lbm.LBM_TAU2_PRINTED, "LBM_TAU2_MAGIC": lbm.LBM_TAU2_MAGIC}
+    assert set(lbm.TAU2_READINGS.values()) == set(t2.values())
+
+
+def test_opts_struct_size_matches(lib):
+    """lbm_default_opts clears sizeof(lbm_opts) bytes: a sentinel just past
+    the binding's struct must survive (the binding's layout is not shorter
+    than the library's), and the defaults land in the binding's fields."""
+    n = ctypes.sizeof(lbm.lbm_opts)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    lib.lbm_default_opts(ctypes.cast(buf, ctypes.POINTER(lbm.lbm_opts)))
+    assert all(b == 0xAB for b in bytes(buf)[n:])
+    o = lbm.lbm_opts.from_buffer_copy(bytes(buf)[:n])
+    assert (o.collision, o.tau2_reading, o.reserved, o.autotune) == (0, 0, 0, 1)
+
+
+@pytest.mark.parametrize("field,value", [("collision", 5), ("collision", -1),
+                                         ("tau2_reading", 2), ("reserved", 1)])
+def test_required_bytes_rejects_bad_options(lib, field, value):
+    o = lbm.lbm_default_opts()
+    setattr(o, field, value)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_required_bytes(lbm.LBM_D2Q9, [8, 8], o)
+    assert e.value.code == lbm.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("coll", [0, 1, 2, 3, 4])
+def test_every_collision_is_accepted(lib, coll):
+    o = lbm.lbm_default_opts()
+    o.collision = coll
+    o.tau2_reading = lbm.LBM_TAU2_MAGIC
+    assert lbm.lbm_required_bytes(lbm.LBM_D2Q9, [8, 8], o) > 0
