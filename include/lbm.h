@@ -204,9 +204,14 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
 
 /* Launch shape in use: out[0] = nodes per thread, out[1] = tile width in
  * thread chunks, out[2] = tile height in rows, out[3] = grid size (CTAs),
- * out[4] = kernel kind (0: register-chunk kernel; 1: shared-memory staged
- * D2Q9 kernel, node pairs per thread, tile width 64/128/256 nodes chosen per
- * instance -- out[1] and out[2] are 0 then). */
+ * out[4] = kernel kind (0: register-chunk kernel; 1: TMA-staged D2Q9 kernel
+ * with large tiles, 2048 nodes for 2-byte storage or 1024 for FP32, on a
+ * two-stage ring; 2: the same kernel with small tiles, 1024 / 512 nodes, on
+ * a three-stage ring.  For kinds 1 and 2 the tile width is 64/128/256 nodes
+ * chosen per instance and out[1], out[2] are 0).  Selection: the create-time
+ * autotuner, or the environment variable LBM_SHAPE = "V,tw,th" (register
+ * chunks), "smem" (kind 1, node pairs), "smem1" (kind 1, single nodes) or
+ * "smems" (kind 2). */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* out);
 
 /* Destroy a context (NULL-safe).  Frees library-owned memory only. */

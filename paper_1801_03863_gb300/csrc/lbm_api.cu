@@ -27,8 +27,9 @@ constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even)
 size_t dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
 
 // Launch shape.  kind 0: register-chunk kernel (V nodes per thread, tiles of
-// tw x th chunks); kind 1: shared-memory staged D2Q9 kernel (node pairs,
-// tiles of smem_tile_nodes() nodes, width per instance).
+// tw x th chunks); kind 1 / 2: TMA-staged D2Q9 kernel with V = P nodes per
+// unit and large / small tiles (smem_tile_nodes variant kind - 1), tile
+// width per instance.
 struct Shape {
     int V, tw, th;
     int kind = 0;
@@ -43,8 +44,9 @@ std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, in
     else vs = {4, 8};
     std::vector<Shape> out;
     if (lattice == 2 && storage != DT_F64) {
-        out.push_back({2, 0, 0, 1});  // shared-memory staged kernel, node pairs
-        out.push_back({1, 0, 0, 1});  // shared-memory staged kernel, single nodes
+        out.push_back({2, 0, 0, 1});  // TMA-staged kernel, node pairs, large tiles
+        out.push_back({1, 0, 0, 1});  // TMA-staged kernel, single nodes, large tiles
+        out.push_back({2, 0, 0, 2});  // TMA-staged kernel, node pairs, small tiles
     }
     for (int V : vs) {
         for (int block : {128, 256}) {
@@ -70,9 +72,10 @@ Shape default_shape(int lattice, int storage) {
 int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const Shape& s,
                     int storage) {
     int64_t n = 0;
-    if (s.kind == 1) {
+    if (s.kind >= 1) {
         for (auto& d : dims) {
-            const int64_t X = smem_tile_width(d.first), R = smem_tile_nodes(storage) / X;
+            const int64_t X = smem_tile_width(d.first);
+            const int64_t R = smem_tile_nodes(storage, s.kind - 1) / X;
             n += ((d.first + X - 1) / X) * ((d.second + R - 1) / R);
         }
         return n;
@@ -122,7 +125,8 @@ Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t
         const int64_t chunks = (d.first + 1) / 2;
         bound += chunks * d.second / 128 + chunks / 4 + d.second + 1;
     }
-    L.max_tiles = std::max(bound, count_tiles(dims, Shape{2, 0, 0, 1}, storage));
+    L.max_tiles = std::max({bound, count_tiles(dims, Shape{2, 0, 0, 1}, storage),
+                            count_tiles(dims, Shape{2, 0, 0, 2}, storage)});
     return L;
 }
 
@@ -177,7 +181,7 @@ struct lbm_ctx {
     double* d_stage = nullptr;
     CUtensorMapOpaque* d_tmaps = nullptr;  // [buffer][instance]
     unsigned int* d_error = nullptr;
-    bool tmaps_ready = false;
+    int tmaps_variant = -1;  // tile variant the TMA tensor maps were built for
     std::vector<TileDesc> tiles;
     bool initialized = false;
     bool post = false;  // stored field is post-collision
@@ -232,10 +236,11 @@ AuxArgs aux_args(const lbm_ctx* ctx) {
 
 std::vector<TileDesc> build_tiles(const lbm_ctx* ctx, const Shape& s) {
     std::vector<TileDesc> t;
-    if (s.kind == 1) {
+    if (s.kind >= 1) {
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
-            const int X = smem_tile_width(in.nx), R = smem_tile_nodes(ctx->storage) / X;
+            const int X = smem_tile_width(in.nx);
+            const int R = smem_tile_nodes(ctx->storage, s.kind - 1) / X;
             for (int64_t y0 = 0; y0 < in.ny; y0 += R)
                 for (int64_t x0 = 0; x0 < in.nx; x0 += X)
                     t.push_back({(int32_t)i, (int32_t)x0, (int32_t)y0, (int32_t)X});
@@ -258,20 +263,21 @@ int ilog2(int v) {
     return r;
 }
 
-int build_tensor_maps(lbm_ctx* ctx);
+int build_tensor_maps(lbm_ctx* ctx, int variant);
 
 // Make shape s current: tile table to the device, kernel and grid size.
 int apply_shape(lbm_ctx* ctx, const Shape& s) {
     const void* k = nullptr;
     size_t smem = 0;
-    if (s.kind == 1) {
-        if (ctx->lattice != 2 || ctx->compute != DT_F32) return LBM_ERR_ARG;
-        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, s.V, &smem);
-        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, s.V, &smem);
-        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, s.V, &smem);
+    if (s.kind >= 1) {
+        if (ctx->lattice != 2 || ctx->compute != DT_F32 || s.kind > 2) return LBM_ERR_ARG;
+        const int var = s.kind - 1;
+        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, s.V, var, &smem);
+        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, s.V, var, &smem);
+        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, s.V, var, &smem);
         if (!k) return LBM_ERR_ARG;
         LBM_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int rc = build_tensor_maps(ctx);
+        const int rc = build_tensor_maps(ctx, var);
         if (rc != LBM_OK) return rc;
     } else {
         k = find_step_kernel(ctx->lattice, ctx->storage, ctx->collision, s.V);
@@ -293,7 +299,7 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     LBM_CK(cudaMemcpyAsync(ctx->d_inst, ctx->layout.inst.data(), sizeof(InstDesc) * ctx->count,
                            cudaMemcpyHostToDevice, ctx->stream));
     LBM_CK(cudaStreamSynchronize(ctx->stream));
-    const int block = s.kind == 1 ? 256 : s.tw * s.th;
+    const int block = s.kind >= 1 ? 256 : s.tw * s.th;
     int per_sm = 0;
     LBM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     per_sm = std::max(per_sm, 1);
@@ -313,8 +319,8 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
 // TMA tensor maps of both population buffers: per instance a 4-D view
 // (element within a 16-byte chunk, chunk, row, plane) with a box of one
 // tile of the staged kernel plus a one-chunk halo on each side in x.
-int build_tensor_maps(lbm_ctx* ctx) {
-    if (ctx->tmaps_ready) return LBM_OK;
+int build_tensor_maps(lbm_ctx* ctx, int variant) {
+    if (ctx->tmaps_variant == variant) return LBM_OK;
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -327,7 +333,7 @@ int build_tensor_maps(lbm_ctx* ctx) {
     EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
     const size_t es = dtype_bytes(ctx->storage);
     const int E = (int)(16 / es);
-    const int tile_nodes = smem_tile_nodes(ctx->storage);
+    const int tile_nodes = smem_tile_nodes(ctx->storage, variant);
     std::vector<CUtensorMap> maps(2 * (size_t)ctx->count);
     for (int b = 0; b < 2; ++b) {
         for (int i = 0; i < ctx->count; ++i) {
@@ -353,7 +359,7 @@ int build_tensor_maps(lbm_ctx* ctx) {
     LBM_CK(cudaMemcpyAsync(ctx->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
                            cudaMemcpyHostToDevice, ctx->stream));
     LBM_CK(cudaStreamSynchronize(ctx->stream));
-    ctx->tmaps_ready = true;
+    ctx->tmaps_variant = variant;
     return LBM_OK;
 }
 
@@ -377,7 +383,7 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
 cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
     StepArgs a = step_args(ctx, src);
     void* params[] = {&a};
-    const int block = ctx->shape.kind == 1 ? 256 : ctx->shape.tw * ctx->shape.th;
+    const int block = ctx->shape.kind >= 1 ? 256 : ctx->shape.tw * ctx->shape.th;
     return cudaLaunchKernel(ctx->kern, dim3(ctx->grid), dim3(block), params, ctx->smem, s);
 }
 
@@ -423,6 +429,10 @@ bool parse_shape_env(Shape* s) {
     }
     if (strcmp(e, "smem1") == 0) {
         *s = {1, 0, 0, 1};
+        return true;
+    }
+    if (strcmp(e, "smems") == 0) {
+        *s = {2, 0, 0, 2};
         return true;
     }
     int v, tw, th;

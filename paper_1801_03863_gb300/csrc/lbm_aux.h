@@ -46,18 +46,30 @@ const void* step_kernel_bf16(int lattice, int collision, int V);
 
 // D2Q9 step kernels with shared-memory tile staging (FP32 arithmetic); also
 // return the dynamic shared memory they need.
-const void* step_kernel_smem_f32(int collision, int P, size_t* smem_bytes);
-const void* step_kernel_smem_f16(int collision, int P, size_t* smem_bytes);
-const void* step_kernel_smem_bf16(int collision, int P, size_t* smem_bytes);
+const void* step_kernel_smem_f32(int collision, int P, int variant, size_t* smem_bytes);
+const void* step_kernel_smem_f16(int collision, int P, int variant, size_t* smem_bytes);
+const void* step_kernel_smem_bf16(int collision, int P, int variant, size_t* smem_bytes);
 // Tile geometry of those kernels: nodes per tile for a storage type, and
 // the tile width for an instance of width nx.
 #ifndef LBM_SMEM_TILE2
-#define LBM_SMEM_TILE2 1024
+#define LBM_SMEM_TILE2 2048
 #endif
 #ifndef LBM_SMEM_TILE4
-#define LBM_SMEM_TILE4 512
+#define LBM_SMEM_TILE4 1024
 #endif
-inline int smem_tile_nodes(int storage) { return storage == 1 ? LBM_SMEM_TILE4 : LBM_SMEM_TILE2; }
+#ifndef LBM_SMEM_TILE2_SMALL
+#define LBM_SMEM_TILE2_SMALL 1024
+#endif
+#ifndef LBM_SMEM_TILE4_SMALL
+#define LBM_SMEM_TILE4_SMALL 512
+#endif
+// Nodes per tile of the TMA-staged kernel: variant 0 = large tiles (fewer
+// per-tile costs, for arithmetic-bound rules), 1 = small tiles with a deeper
+// ring (more copies in flight, for bandwidth-bound rules).
+inline int smem_tile_nodes(int storage, int variant) {
+    if (variant == 1) return storage == 1 ? LBM_SMEM_TILE4_SMALL : LBM_SMEM_TILE2_SMALL;
+    return storage == 1 ? LBM_SMEM_TILE4 : LBM_SMEM_TILE2;
+}
 inline int smem_tile_width(int64_t nx) { return nx >= 256 ? 256 : (nx >= 128 ? 128 : 64); }
 
 }  // namespace lbm

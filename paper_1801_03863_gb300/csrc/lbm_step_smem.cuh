@@ -6,36 +6,42 @@
 //
 //  * A CTA (256 threads) walks the tile table of the context; a tile is X
 //    nodes (64, 128 or 256, chosen per instance) by R = TILE_NODES / X rows.
+//    Two geometries are compiled: large tiles (2048 nodes for 2-byte storage,
+//    1024 for 4-byte) with a two-stage ring, which halve the per-tile costs
+//    of arithmetic-bound rules, and small tiles (1024 / 512) with a
+//    three-stage ring, which keep more copies in flight for bandwidth-bound
+//    ones; the autotuner picks per context.
 //  * Each instance's populations are described to TMA as a 4-D tensor
 //    (element within a 16-byte chunk, chunk, row, plane).  For every plane
 //    one elected thread issues a single tensor copy of the tile's rows
 //    shifted by -v_y, one chunk wider on each side in x (the halo); copies
 //    outside the lattice are zero-filled by the hardware, which is exactly
 //    the cavity's "outside" value (deviation 0).
-//  * A two-stage shared-memory ring with one mbarrier per stage: the copies
-//    of tile k+1 are in flight while tile k is collided.  Every wait is
-//    bounded; on timeout the kernel records an error word and the CTA leaves
-//    after a bounded wait for its own copies still in flight.
-//  * Halo values a zero fill cannot express (periodic wrap, zero-gradient
-//    copies of the element beyond an end) are patched in shared memory.
-//  * Each thread collides one node pair per row (packed FP32x2 arithmetic),
-//    reading 4-byte words from shared memory (consecutive threads,
-//    consecutive words: no bank conflicts) and storing each plane's pair
-//    with one 4- or 8-byte store (a warp writes 128 or 256 contiguous bytes).
+//  * A ring of STAGES shared-memory stages, each with a "full" mbarrier (the
+//    copies landed) and an "empty" one (every warp is done with it): the
+//    copies of the next tiles are in flight while one is collided.  Every
+//    wait is bounded; on timeout the kernel records an error word and the
+//    CTA leaves after a bounded wait for its own copies still in flight.
+//  * Nodes whose pull crosses a periodic or zero-gradient edge, which a zero
+//    fill cannot express, read their neighbours from global memory with the
+//    boundary rule.
+//  * Each thread collides one node pair (packed FP32x2 arithmetic) or one
+//    node per unit, reading 4-byte words from shared memory (consecutive
+//    threads, consecutive words: no bank conflicts) and storing each plane's
+//    pair with one 4- or 8-byte store (a warp writes 128 or 256 contiguous
+//    bytes).
 #pragma once
+#include "lbm_aux.h"
 #include "lbm_collide.cuh"
 #include "lbm_step.cuh"
 
 namespace lbm {
 
-#ifndef LBM_SMEM_TILE2
-#define LBM_SMEM_TILE2 1024  // nodes per tile, 2-byte storage
-#endif
-#ifndef LBM_SMEM_TILE4
-#define LBM_SMEM_TILE4 512   // nodes per tile, 4-byte storage
-#endif
 #ifndef LBM_SMEM_STAGES
-#define LBM_SMEM_STAGES 3    // depth of the shared-memory ring
+#define LBM_SMEM_STAGES 2        // ring depth, large tiles
+#endif
+#ifndef LBM_SMEM_STAGES_SMALL
+#define LBM_SMEM_STAGES_SMALL 3  // ring depth, small tiles
 #endif
 
 template <typename S, int TILE = (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4),
@@ -64,7 +70,7 @@ struct SmemTile {
 // before it arms the stage's barrier (consumers read them after the wait).
 struct StageParams {
     int64_t off, pitch, plane;
-    int32_t inst, X, x0, y0, nx, ny, bc, R;
+    int32_t inst, X, x0, y0, nx, ny, bc, R, xl2;  // xl2 = log2(X)
     float omega, omega2, s_e, s_eps;
     float lid[9];
 };
@@ -225,7 +231,7 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
 #endif
 
 #ifndef LBM_SMEM_MINBLOCKS1
-#define LBM_SMEM_MINBLOCKS1 3  // resident CTAs per SM, one-node-per-thread variant
+#define LBM_SMEM_MINBLOCKS1 2  // resident CTAs per SM, one-node-per-thread variant
 #endif
 
 // P = nodes per thread and row: 2 (node pairs, packed FP32x2 arithmetic) or
@@ -278,6 +284,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
         p.off = in.off; p.pitch = in.pitch; p.plane = in.plane;
         p.inst = tile.inst; p.X = tile.pad; p.x0 = tile.cx0; p.y0 = tile.y0;
         p.nx = in.nx; p.ny = in.ny; p.bc = in.bc; p.R = TS::TILE_NODES / tile.pad;
+        p.xl2 = 31 - __clz(tile.pad);
         p.omega = (float)in.omega;
         p.omega2 = (float)in.omega2;
         p.s_e = (float)in.s_e;
@@ -315,16 +322,16 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
         jdone = j;
 
         const StageParams& p = params[st];
-        const int X = p.X, R = p.R;
+        const int X = p.X;
         const int SP = X + 2 * E;  // smem row length (elements)
         const int x0 = p.x0, y0 = p.y0, nx = p.nx, ny = p.ny, bc = p.bc;
         const int64_t pitch = p.pitch, plane = p.plane, off = p.off;
         S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
 
-        const int pcols = X / P;                  // thread columns per row
-        const int px = tid & (pcols - 1);
-        const int rg = tid / pcols;               // first row of this thread
-        const int rstep = TS::THREADS / pcols;    // rows between this thread's units
+        const int cl2 = p.xl2 - (P == 2 ? 1 : 0);  // log2 of the thread columns per row
+        const int px = tid & ((1 << cl2) - 1);
+        const int rg = tid >> cl2;                  // first row of this thread
+        const int rstep = TS::THREADS >> cl2;       // rows between this thread's units
         const int x = x0 + P * px;
         // own position in a shared row: element E + P px (in words for pairs
         // of 2-byte types)
@@ -341,6 +348,10 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
             for (int a = 0; a < Q; ++a) lid[a] = p.lid[a];
         }
         const int inst = p.inst;
+        // this thread's output position in its first row; advanced by rstep
+        // rows per unit
+        S* orow = dst + off + (int64_t)(y0 + rg) * pitch + x;
+        const int64_t ostep = (int64_t)rstep * pitch;
 #ifdef LBM_SMEM_INTERLEAVE
 #pragma unroll
 #else
@@ -349,6 +360,8 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
         for (int k = 0; k < MAXP; ++k) {
             const int r = rg + k * rstep;
             const int y = y0 + r;
+            S* op = orow;
+            orow += ostep;
             CT d[Q];
             {
                 const S* srow = sbase + r * SP;
@@ -394,15 +407,13 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
             n_skip += (sts & ST_NEWTON_SKIPPED) + ((sts >> 2) & ST_NEWTON_SKIPPED);
             n_unst += ((sts & ST_UNSTABLE) >> 1) + (((sts >> 2) & ST_UNSTABLE) >> 1);
             if constexpr (P == 1) {
-                S* op1 = dst + off + (int64_t)y * pitch + x;
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    store_elem<S>(op1, o[a].v);
-                    op1 += plane;
+                    store_elem<S>(op, o[a].v);
+                    op += plane;
                 }
                 continue;
             } else {
-            S* op = dst + off + (int64_t)y * pitch + x;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 store_pair<S>(op, o[a].v.x, o[a].v.y, second);
@@ -428,14 +439,16 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
     }
 }
 
-// The TMA-staged D2Q9 kernel for a collision rule, P nodes per unit, with
-// the default tile geometry of storage S; *smem_bytes receives its dynamic
-// shared memory size.
-template <typename S, int P>
+// The TMA-staged D2Q9 kernel for a collision rule, P nodes per unit and
+// tile geometry VARIANT (0: large tiles, 1: small tiles, see
+// smem_tile_nodes); *smem_bytes receives its dynamic shared memory size.
+template <typename S, int P, int VARIANT>
 const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
-    using TS = SmemTile<S>;
+    constexpr int TN = VARIANT == 0 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4)
+                                    : (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL);
+    constexpr int NS = VARIANT == 0 ? LBM_SMEM_STAGES : LBM_SMEM_STAGES_SMALL;
+    using TS = SmemTile<S, TN, NS>;
     *smem_bytes = TS::SMEM_BYTES;
-    constexpr int TN = TS::TILE_NODES, NS = TS::STAGES;
     switch (collision) {
         case COLL_MINXENT4: return (const void*)&step_kernel_smem<S, COLL_MINXENT4, TN, NS, P>;
         case COLL_SRT: return (const void*)&step_kernel_smem<S, COLL_SRT, TN, NS, P>;

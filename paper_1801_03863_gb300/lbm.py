@@ -233,7 +233,7 @@ def lbm_launch_shape(h) -> dict:
     c = np.zeros(5, np.int32)
     _check(load().lbm_launch_shape(h, _p(c)), "lbm_launch_shape")
     return {"V": int(c[0]), "tw": int(c[1]), "th": int(c[2]), "grid": int(c[3]),
-            "kind": "smem" if c[4] == 1 else "chunks"}
+            "kind": {0: "chunks", 1: "smem", 2: "smem_small"}[int(c[4])]}
 
 
 def lbm_destroy(h) -> None:
