@@ -160,10 +160,9 @@ __device__ __forceinline__ void store_elem(S* p, float a) {
     *p = Store<S>::from(a);
 }
 
-// Store one pair (lane 1 dropped when it lies beyond the row: padding stays 0).
+// Store one pair.
 template <typename S>
-__device__ __forceinline__ void store_pair(S* p, float a, float b, bool second_valid) {
-    if (!second_valid) b = 0.f;
+__device__ __forceinline__ void store_pair(S* p, float a, float b) {
     if constexpr (std::is_same<S, __half>::value) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
     } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
@@ -368,7 +367,9 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                 load_unit<S, P>(srow, wb, TS::PLANE_ELEMS, d);
             }
             if (y >= ny || !xin) continue;
-            if (bc != BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
+            // node (pair) on the lattice's outer ring: boundary rules apply
+            const bool edge = (y == 0) | (y == ny - 1) | xedge;
+            if (edge && bc != BC_CAVITY) {
                 const S* gb = src + off;
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
             }
             CT o[Q];
             uint32_t sts = Collide<D2Q9, COLL, CT>::run(d, rho0v, rates, o);
-            if (bc == BC_CAVITY && (y == 0 || y == ny - 1 || xedge)) {
+            if (edge && bc == BC_CAVITY) {
 #pragma unroll
                 for (int l = 0; l < P; ++l) {
                     const int xl2 = x + l;
@@ -403,22 +404,29 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                     }
                 }
             }
-            if (!second) sts &= 3u;
-            n_skip += (sts & ST_NEWTON_SKIPPED) + ((sts >> 2) & ST_NEWTON_SKIPPED);
-            n_unst += ((sts & ST_UNSTABLE) >> 1) + (((sts >> 2) & ST_UNSTABLE) >> 1);
+            if (sts) {  // rare: some lane skipped its Newton step or is unstable
+                if (!second) sts &= 3u;
+                n_skip += __popc(sts & (ST_NEWTON_SKIPPED * 5u));
+                n_unst += __popc(sts & (ST_UNSTABLE * 5u));
+            }
             if constexpr (P == 1) {
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
                     store_elem<S>(op, o[a].v);
                     op += plane;
                 }
-                continue;
             } else {
+                // the second node of a pair beyond the row (odd widths) is
+                // row padding: keep it zero
+                if (!second) {
 #pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                store_pair<S>(op, o[a].v.x, o[a].v.y, second);
-                op += plane;
-            }
+                    for (int a = 0; a < Q; ++a) o[a].v.y = 0.f;
+                }
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    store_pair<S>(op, o[a].v.x, o[a].v.y);
+                    op += plane;
+                }
             }
         }
         __syncwarp();
