@@ -248,8 +248,10 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the step kernels are compiled from."""
     h = hashlib.sha256()
-    for f in ("lbm_step.cuh", "lbm_collide.cuh", "lbm_common.cuh"):
+    for f in ("lbm_common.cuh", "lbm_num.cuh", "lbm_collide.cuh", "lbm_step.cuh",
+              "lbm_step_smem.cuh", "lbm_aux.h"):
         h.update(open(os.path.join(ROOT, "paper_1801_03863_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -193,12 +193,13 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     const T c8 = (T(9.0) * k) * N::mad(pxx, ir, uyy - uxx);
     const T c9 = (T(36.0) * k) * N::mad(pxy, ir, -(ux * uy));
     // delta_a = p^start_a / W_a - 1
+    const T C1 = T(1.0), C3 = T(3.0), C45 = T(4.5);
     const T b0 = T(-1.5) * (uxx + uyy);
-    const T sx = N::mad(T(4.5), uxx, b0 + c8);
-    const T sy = N::mad(T(4.5), uyy, b0 - c8);
+    const T sx = N::mad(C45, uxx, b0 + c8);
+    const T sy = N::mad(C45, uyy, b0 - c8);
     const T sp_ = ux + uy, dm_ = uy - ux;
-    const T sp = N::mad(T(4.5) * sp_, sp_, b0 + c9);
-    const T sm = N::mad(T(4.5) * dm_, dm_, b0 - c9);
+    const T sp = N::mad(C45 * sp_, sp_, b0 + c9);
+    const T sm = N::mad(C45 * dm_, dm_, b0 - c9);
     T del[9];
     // coefficients of the terms odd in v: 3 v.u, plus for MinxEnt2 the
     // relaxed heat flux, T_5a g_x / (12 W_a) = (-3/2 on +x, +3 on (+,+) ...)
@@ -216,19 +217,19 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         lm = dm_ + (gy - gx);
     }
     del[0] = b0;
-    del[1] = N::mad(T(3.0), hx, sx);
-    del[3] = N::mad(T(-3.0), hx, sx);
-    del[2] = N::mad(T(3.0), hy, sy);
-    del[4] = N::mad(T(-3.0), hy, sy);
-    del[5] = N::mad(T(3.0), lp, sp);
-    del[7] = N::mad(T(-3.0), lp, sp);
-    del[6] = N::mad(T(3.0), lm, sm);
-    del[8] = N::mad(T(-3.0), lm, sm);
+    del[1] = N::mad(C3, hx, sx);
+    del[3] = N::mad(-C3, hx, sx);
+    del[2] = N::mad(C3, hy, sy);
+    del[4] = N::mad(-C3, hy, sy);
+    del[5] = N::mad(C3, lp, sp);
+    del[7] = N::mad(-C3, lp, sp);
+    del[6] = N::mad(C3, lm, sm);
+    del[8] = N::mad(-C3, lm, sm);
 
     // y_a = p^start_a / W_a; all positive <=> the logarithms exist (reading C-NEG)
     T y[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) y[a] = T(1.0) + del[a];
+    for (int a = 0; a < 9; ++a) y[a] = C1 + del[a];
     // FP64: the exact test of reading C-NEG.  FP32: see the Newton-step test below.
     typename N::Pred ok{};
     if constexpr (std::is_same<T, double>::value) {
