@@ -85,6 +85,7 @@ def _load():
             "orc_conservation": (None, [P, P]),
             "orc_counters": (None, [P, P]),
             "orc_num_threads": (I, []),
+            "orc_stream_function": (None, [I, I, P, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -215,6 +216,16 @@ def num_threads() -> int:
 # --------------------------------------------------------------------------
 # Lattice simulation (Eq. 2 with the boundary rules of Sec. IV.F).
 # --------------------------------------------------------------------------
+def stream_function(uy) -> np.ndarray:
+    """Sec. IV.I stream function psi = -int_0^x u_y dx per row (lattice
+    units; Simpson over pairs of intervals, trapezoid on a last odd one)."""
+    uy = _f64(uy)
+    ny, nx = uy.shape
+    out = np.zeros((ny, nx))
+    _load().orc_stream_function(int(nx), int(ny), _ptr(uy), _ptr(out))
+    return out
+
+
 class Sim:
     """One oracle lattice.  Arrays are [y][x] (x fastest); populations [a][y][x]."""
 

@@ -756,6 +756,34 @@ ORC_EXPORT void orc_counters(const orc_sim* s, long long* out) {
     out[2] = s->steps;
 }
 
+/*
+ * Stream function of the LDAS post-processing (Sec. IV.I):
+ *   psi(x, y) = - integral from the left wall (x = 0) to x of u_y dx,
+ * evaluated along each row in lattice units (node spacing 1).  The integral
+ * over [0, x] uses the composite Simpson rule on the pairs of intervals
+ * [0, 2], [2, 4], ...; at odd x the last interval [x - 1, x] uses the
+ * trapezoidal rule (the paper integrates with Simpson's rule where the
+ * spacing allows it and with the trapezoid elsewhere).
+ *   uy   [ny][nx] vertical velocity
+ *   psi  [ny][nx] output
+ */
+ORC_EXPORT void orc_stream_function(int nx, int ny, const double* uy, double* psi) {
+    for (int y = 0; y < ny; ++y) {
+        const double* u = uy + (size_t)y * nx;
+        double* p = psi + (size_t)y * nx;
+        double simpson = 0.0; /* integral over [0, x] for the last even x */
+        p[0] = 0.0;
+        for (int x = 1; x < nx; ++x) {
+            if (x % 2 == 0) {
+                simpson += (u[x - 2] + 4.0 * u[x - 1] + u[x]) / 3.0;
+                p[x] = -simpson;
+            } else {
+                p[x] = -(simpson + 0.5 * (u[x - 1] + u[x]));
+            }
+        }
+    }
+}
+
 ORC_EXPORT int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

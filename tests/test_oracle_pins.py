@@ -431,3 +431,45 @@ def test_taylor_green_decay_low_viscosity(orc):
     rate_srt, _ = _tg_rate(orc, 64, 1e-3, 2000, 1)
     assert rate == pytest.approx(expect, rel=3e-2)
     assert rate == pytest.approx(rate_srt, rel=2e-3)
+
+
+# ----------------------------------------------------------------------------
+# Stream function of the LDAS post-processing (Sec. IV.I).
+# ----------------------------------------------------------------------------
+def test_stream_function_closed_forms(orc):
+    """psi = -int_0^x u_y dx per row with composite Simpson over pairs of
+    unit intervals and the trapezoid on a last odd interval:
+      u = a + b x  -> exact:            -(a x + b x^2 / 2)
+      u = x^2      -> Simpson exact at even x (-x^3/3); at odd x the
+                      trapezoid over [x-1, x] adds 1/6:  -(x^3/3 + 1/6)
+      u = x^3      -> Simpson exact at even x:          -x^4/4."""
+    nx = 21
+    x = np.arange(nx, dtype=float)
+    uy = np.stack([0.3 - 0.05 * x, x ** 2, x ** 3])
+    psi = orc.stream_function(uy)
+    np.testing.assert_allclose(psi[0], -(0.3 * x - 0.025 * x ** 2), rtol=0, atol=1e-13)
+    even, odd = x[0::2], x[1::2]
+    np.testing.assert_allclose(psi[1, 0::2], -even ** 3 / 3, rtol=1e-14, atol=1e-12)
+    np.testing.assert_allclose(psi[1, 1::2], -(odd ** 3 / 3 + 1 / 6), rtol=1e-14, atol=1e-12)
+    np.testing.assert_allclose(psi[2, 0::2], -even ** 4 / 4, rtol=1e-14, atol=1e-12)
+
+
+def test_stream_function_matches_library_simpson_and_converges(orc):
+    """At even x the rule is the composite Simpson rule of scipy; for a
+    smooth profile the error falls as h^4."""
+    integrate = pytest.importorskip("scipy.integrate")
+    rng = np.random.default_rng(4)
+    uy = rng.standard_normal((3, 33))
+    psi = orc.stream_function(uy)
+    for k in range(2, 33, 2):
+        ref = -integrate.simpson(uy[:, :k + 1], dx=1.0, axis=1)
+        np.testing.assert_allclose(psi[:, k], ref, rtol=1e-12, atol=1e-12)
+    errs = []
+    for n in (17, 33, 65):
+        L = n - 1
+        x = np.arange(n, dtype=float)
+        u = np.sin(np.pi * x / L)[None, :]
+        exact = -(L / np.pi) * (1 - np.cos(np.pi * x / L))
+        # error relative to the integral's scale L (spacing h = 1/L)
+        errs.append(np.abs(orc.stream_function(u)[0, 0::2] - exact[0::2]).max() / L)
+    assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14, errs
