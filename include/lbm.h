@@ -161,6 +161,20 @@ int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy);
  * no status check. */
 int lbm_moments_device(lbm_ctx* ctx, double* rho, double* ux, double* uy);
 
+/* Stream function of f(x, t_n) for the lid-driven cavity analysis of
+ * Sec. IV.I: per row of every instance, psi(x, y) = - integral from x = 0 to
+ * x of u_y dx, in lattice units (node spacing 1, psi = 0 at x = 0), with the
+ * composite Simpson rule over pairs of unit intervals and the trapezoidal
+ * rule on a last odd interval.  psi: host FP64 array of sum(nx*ny) values in
+ * the order of lbm_moments (per instance [y][x]).  D2Q9 only (LBM_ERR_ARG
+ * otherwise).  Synchronises; status as lbm_moments.  Normalise by
+ * |u_lid| (side - 1) for the paper's psi-hat. */
+int lbm_stream_function(lbm_ctx* ctx, double* psi);
+
+/* lbm_stream_function into a DEVICE FP64 array, ordered on the stream, no
+ * sync and no status check (uses the context's staging area for u). */
+int lbm_stream_function_device(lbm_ctx* ctx, double* psi);
+
 /* Populations f(x, t_n) to / from host FP64, layout per instance
  * [a][y][x] (a in the order rest, +x, +y, -x, -y, (+x,+y), (-x,+y),
  * (-x,-y), (+x,-y) for D2Q9; rest, +x, -x for D1Q3), instances

@@ -728,6 +728,35 @@ int lbm_moments_device(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
     return LBM_OK;
 }
 
+int lbm_stream_function_device(lbm_ctx* ctx, double* psi) {
+    if (!ctx || !psi) return LBM_ERR_ARG;
+    if (ctx->Q != 9) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    const size_t n = (size_t)ctx->layout.total_nodes;
+    AuxArgs a = aux_args(ctx);
+    // u_y of f(t_n) into the staging area (rho and u_x beside it), then the
+    // row integrals
+    LBM_CK(run_aux(AuxOp::Moments, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr,
+                   ctx->d_stage, ctx->d_stage + n, ctx->d_stage + 2 * n));
+    LBM_CK(stream_function(a, ctx->layout.max_ny, ctx->d_stage + 2 * n, psi));
+    return LBM_OK;
+}
+
+int lbm_stream_function(lbm_ctx* ctx, double* psi) {
+    if (!ctx || !psi) return LBM_ERR_ARG;
+    const size_t n = (size_t)ctx->layout.total_nodes;
+    double* dpsi = ctx->d_stage + 3 * n;
+    int rc = lbm_stream_function_device(ctx, dpsi);
+    if (rc != LBM_OK) return rc;
+    LBM_CK(cudaMemcpyAsync(psi, dpsi, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    int64_t c[3];
+    rc = lbm_status(ctx, c);
+    if (rc != LBM_OK) return rc;
+    return c[1] ? LBM_ERR_UNSTABLE : LBM_OK;
+}
+
 int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters) {
     if (!ctx || !counters || instance < 0 || instance >= ctx->count) return LBM_ERR_ARG;
     if (ctx->failed) return LBM_ERR_CUDA;

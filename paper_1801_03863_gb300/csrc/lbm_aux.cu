@@ -3,6 +3,8 @@
 // population read-out, population load, and the FP64 conservation
 // reduction.  One thread per node, grid = (blocks, instance); none of these
 // is on the per-step hot path.
+#include <algorithm>
+
 #include "lbm_aux.h"
 #include "lbm_collide.cuh"
 
@@ -358,12 +360,45 @@ cudaError_t aux_by_storage(AuxOp op, const AuxArgs& a, const void* src, void* ds
     return cudaErrorInvalidValue;
 }
 
+// Stream function of the LDAS post-processing (Sec. IV.I) along each row of
+// each instance: psi(x, y) = - integral_0^x u_y dx in lattice units, with
+// the composite Simpson rule over pairs of unit intervals from the left
+// wall and the trapezoidal rule on the last interval when x is odd.  One
+// thread per row (rows of instance blockIdx.y).
+__global__ void stream_function_kernel(const double* __restrict__ uy,
+                                       const InstDesc* __restrict__ insts, double* __restrict__ psi) {
+    const InstDesc& in = insts[blockIdx.y];
+    const int nx = in.nx;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < in.ny; y += gridDim.x * blockDim.x) {
+        const double* u = uy + in.node0 + (int64_t)y * nx;
+        double* p = psi + in.node0 + (int64_t)y * nx;
+        double simpson = 0.0;  // integral over [0, x] at the last even x
+        p[0] = 0.0;
+        for (int x = 1; x < nx; ++x) {
+            if (x & 1) {
+                p[x] = -(simpson + 0.5 * (u[x - 1] + u[x]));
+            } else {
+                simpson += (u[x - 2] + 4.0 * u[x - 1] + u[x]) * (1.0 / 3.0);
+                p[x] = -simpson;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t run_aux(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
                     const double* p1, const double* p2, double* o0, double* o1, double* o2) {
     if (a.lattice == 2) return aux_by_storage<D2Q9>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
     return aux_by_storage<D1Q3>(op, a, src, dst, p0, p1, p2, o0, o1, o2);
+}
+
+cudaError_t stream_function(const AuxArgs& a, int64_t max_ny, const double* uy, double* psi) {
+    const int threads = 128;
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_ny + threads - 1) / threads, 1024)),
+                    (unsigned)a.count);
+    stream_function_kernel<<<grid, threads, 0, a.stream>>>(uy, a.inst, psi);
+    return cudaGetLastError();
 }
 
 }  // namespace lbm

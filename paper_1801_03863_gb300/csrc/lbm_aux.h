@@ -37,6 +37,10 @@ struct AuxArgs {
 cudaError_t run_aux(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
                     const double* p1, const double* p2, double* o0, double* o1, double* o2);
 
+// psi <- stream function of u_y (both [inst][y][x] FP64 device arrays in the
+// concatenated node order); max_ny = largest instance height.
+cudaError_t stream_function(const AuxArgs& a, int64_t max_ny, const double* uy, double* psi);
+
 // Fused step kernels, one translation unit per storage type.  Each returns
 // the __global__ function for (lattice, collision, V), or nullptr.
 const void* step_kernel_f64(int lattice, int collision, int V);

@@ -36,6 +36,7 @@ EXPORTS = (
     "lbm_default_opts", "lbm_required_bytes", "lbm_create", "lbm_create_batch", "lbm_init",
     "lbm_init_device", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_get_populations",
     "lbm_set_populations", "lbm_conservation", "lbm_conservation_device",
+    "lbm_stream_function", "lbm_stream_function_device",
     "lbm_conservation_noalloc", "lbm_status",
     "lbm_status_instance",
     "lbm_launch_shape", "lbm_destroy", "lbm_status_string",
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_step": (ctypes.c_int, [P, I64]),
             "lbm_moments": (ctypes.c_int, [P, P, P, P]),
             "lbm_moments_device": (ctypes.c_int, [P, P, P, P]),
+            "lbm_stream_function": (ctypes.c_int, [P, P]),
+            "lbm_stream_function_device": (ctypes.c_int, [P, P]),
             "lbm_get_populations": (ctypes.c_int, [P, P]),
             "lbm_set_populations": (ctypes.c_int, [P, P]),
             "lbm_conservation": (ctypes.c_int, [P, P]),
@@ -188,6 +191,17 @@ def lbm_moments(h, n_nodes: int, want_uy: bool = True, allow_unstable: bool = Fa
 
 def lbm_moments_device(h, rho_ptr: int, ux_ptr, uy_ptr) -> None:
     _check(load().lbm_moments_device(h, rho_ptr, ux_ptr, uy_ptr), "lbm_moments_device")
+
+
+def lbm_stream_function(h, n_nodes: int, allow_unstable: bool = False) -> np.ndarray:
+    psi = np.empty(n_nodes)
+    _check(load().lbm_stream_function(h, _p(psi)), "lbm_stream_function",
+           allow_unstable=allow_unstable)
+    return psi
+
+
+def lbm_stream_function_device(h, psi_ptr: int) -> None:
+    _check(load().lbm_stream_function_device(h, psi_ptr), "lbm_stream_function_device")
 
 
 def lbm_get_populations(h, n_values: int) -> np.ndarray:
@@ -331,6 +345,13 @@ class Lattice:
     def moments_device(self, rho, ux, uy=None):
         ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
         lbm_moments_device(self._h, ptr(rho), ptr(ux), ptr(uy))
+
+    def stream_function(self, allow_unstable: bool = False) -> np.ndarray:
+        """psi of every instance (lattice units), concatenated like moments()."""
+        return lbm_stream_function(self._h, self.n_nodes, allow_unstable)
+
+    def stream_function_device(self, psi):
+        lbm_stream_function_device(self._h, ctypes.c_void_p(psi.data_ptr()))
 
     def populations(self) -> np.ndarray:
         return lbm_get_populations(self._h, self.n_nodes * self.q)

@@ -99,6 +99,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbm_init(None, None, None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_moments(None, None, None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_conservation(None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_stream_function(None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_stream_function_device(None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_destroy(None) == lbm.LBM_OK
 
 
