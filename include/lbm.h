@@ -224,8 +224,7 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * a three-stage ring.  For kinds 1 and 2 the tile width is 64/128/256 nodes
  * chosen per instance and out[1], out[2] are 0).  Selection: the create-time
  * autotuner, or the environment variable LBM_SHAPE = "V,tw,th" (register
- * chunks), "smem" (kind 1, node pairs), "smem1" (kind 1, single nodes) or
- * "smems" (kind 2). */
+ * chunks), "smem" (kind 1) or "smems" (kind 2). */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* out);
 
 /* Destroy a context (NULL-safe).  Frees library-owned memory only. */

@@ -27,8 +27,8 @@ constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even)
 size_t dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
 
 // Launch shape.  kind 0: register-chunk kernel (V nodes per thread, tiles of
-// tw x th chunks); kind 1 / 2: TMA-staged D2Q9 kernel with V = P nodes per
-// unit and large / small tiles (smem_tile_nodes variant kind - 1), tile
+// tw x th chunks); kind 1 / 2: TMA-staged D2Q9 kernel with node pairs
+// (V = 2) and large / small tiles (smem_tile_nodes variant kind - 1), tile
 // width per instance.
 struct Shape {
     int V, tw, th;
@@ -45,7 +45,6 @@ std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, in
     std::vector<Shape> out;
     if (lattice == 2 && storage != DT_F64) {
         out.push_back({2, 0, 0, 1});  // TMA-staged kernel, node pairs, large tiles
-        out.push_back({1, 0, 0, 1});  // TMA-staged kernel, single nodes, large tiles
         out.push_back({2, 0, 0, 2});  // TMA-staged kernel, node pairs, small tiles
     }
     for (int V : vs) {
@@ -272,9 +271,9 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     if (s.kind >= 1) {
         if (ctx->lattice != 2 || ctx->compute != DT_F32 || s.kind > 2) return LBM_ERR_ARG;
         const int var = s.kind - 1;
-        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, s.V, var, &smem);
-        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, s.V, var, &smem);
-        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, s.V, var, &smem);
+        if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, var, &smem);
+        else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, var, &smem);
+        else if (ctx->storage == DT_BF16) k = step_kernel_smem_bf16(ctx->collision, var, &smem);
         if (!k) return LBM_ERR_ARG;
         LBM_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int rc = build_tensor_maps(ctx, var);
@@ -425,10 +424,6 @@ bool parse_shape_env(Shape* s) {
     if (!e) return false;
     if (strcmp(e, "smem") == 0 || strcmp(e, "smem2") == 0) {
         *s = {2, 0, 0, 1};
-        return true;
-    }
-    if (strcmp(e, "smem1") == 0) {
-        *s = {1, 0, 0, 1};
         return true;
     }
     if (strcmp(e, "smems") == 0) {

@@ -50,9 +50,9 @@ const void* step_kernel_bf16(int lattice, int collision, int V);
 
 // D2Q9 step kernels with shared-memory tile staging (FP32 arithmetic); also
 // return the dynamic shared memory they need.
-const void* step_kernel_smem_f32(int collision, int P, int variant, size_t* smem_bytes);
-const void* step_kernel_smem_f16(int collision, int P, int variant, size_t* smem_bytes);
-const void* step_kernel_smem_bf16(int collision, int P, int variant, size_t* smem_bytes);
+const void* step_kernel_smem_f32(int collision, int variant, size_t* smem_bytes);
+const void* step_kernel_smem_f16(int collision, int variant, size_t* smem_bytes);
+const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes);
 // Tile geometry of those kernels: nodes per tile for a storage type, and
 // the tile width for an instance of width nx.
 #ifndef LBM_SMEM_TILE2

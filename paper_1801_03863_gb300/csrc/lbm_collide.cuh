@@ -124,37 +124,31 @@ __device__ __forceinline__ uint32_t sign_status(const T (&out)[Q], const double 
     return st;
 }
 
-// 4x4 symmetric positive definite solve A x = b by 2x2 blocks:
-//   A = [P B; B^T C],  P, C 2x2,
-//   Schur complement Z = C - B^T P^-1 B (SPD when A is),
-//   x2 = Z^-1 (b2 - B^T P^-1 b1),  x1 = P^-1 (b1 - B x2).
-// Two reciprocals (of det P and det Z) and a short dependency chain.
-// A given as its 10 unique entries, unknown order (1, 2 | 3, 4).
+// 4x4 symmetric positive definite solve A x = b by an LDL^T factorisation:
+// A = L D L^T with unit lower-triangular L, then L z = b, x = L^-T D^-1 z.
+// Four reciprocals (of the pivots) and 32 multiply-adds; A is given as its
+// 10 unique entries, unknown order (1, 2, 3, 4).
 template <typename T>
 __device__ __forceinline__ void spd4_solve(T a11, T a21, T a22, T a31, T a32, T a33, T a41, T a42,
                                            T a43, T a44, T b1, T b2, T b3, T b4, T& x1, T& x2,
                                            T& x3, T& x4) {
     using N = Num<T>;
-    // P^-1 = [a22 -a21; -a21 a11] / det P
-    const T ip = N::rcp(N::mad(a11, a22, -(a21 * a21)));
-    const T p11 = a22 * ip, p12 = -(a21 * ip), p22 = a11 * ip;
-    // W = P^-1 B, B = [a31 a41; a32 a42]
-    const T w11 = N::mad(p11, a31, p12 * a32), w12 = N::mad(p11, a41, p12 * a42);
-    const T w21 = N::mad(p12, a31, p22 * a32), w22 = N::mad(p12, a41, p22 * a42);
-    // Z = C - B^T W
-    const T z11 = a33 - N::mad(a31, w11, a32 * w21);
-    const T z12 = a43 - N::mad(a31, w12, a32 * w22);
-    const T z22 = a44 - N::mad(a41, w12, a42 * w22);
-    const T iz = N::rcp(N::mad(z11, z22, -(z12 * z12)));
-    // y1 = P^-1 b1 ; r2 = b2 - B^T y1
-    const T y1 = N::mad(p11, b1, p12 * b2), y2 = N::mad(p12, b1, p22 * b2);
-    const T r3 = b3 - N::mad(a31, y1, a32 * y2);
-    const T r4 = b4 - N::mad(a41, y1, a42 * y2);
-    // x2 = Z^-1 r2 ; x1 = y1 - W x2
-    x3 = N::mad(z22, r3, -(z12 * r4)) * iz;
-    x4 = N::mad(z11, r4, -(z12 * r3)) * iz;
-    x1 = y1 - N::mad(w11, x3, w12 * x4);
-    x2 = y2 - N::mad(w21, x3, w22 * x4);
+    const T r1 = N::rcp(a11);
+    const T l21 = a21 * r1, l31 = a31 * r1, l41 = a41 * r1;
+    const T r2 = N::rcp(N::mad(-l21, a21, a22));
+    const T t32 = N::mad(-l31, a21, a32), t42 = N::mad(-l41, a21, a42);
+    const T l32 = t32 * r2, l42 = t42 * r2;
+    const T r3 = N::rcp(N::mad(-l32, t32, N::mad(-l31, a31, a33)));
+    const T t43 = N::mad(-l42, t32, N::mad(-l41, a31, a43));
+    const T l43 = t43 * r3;
+    const T r4 = N::rcp(N::mad(-l43, t43, N::mad(-l42, t42, N::mad(-l41, a41, a44))));
+    const T z2 = N::mad(-l21, b1, b2);
+    const T z3 = N::mad(-l32, z2, N::mad(-l31, b1, b3));
+    const T z4 = N::mad(-l43, z3, N::mad(-l42, z2, N::mad(-l41, b1, b4)));
+    x4 = z4 * r4;
+    x3 = N::mad(-l43, x4, z3 * r3);
+    x2 = N::mad(-l42, x4, N::mad(-l32, x3, z2 * r2));
+    x1 = N::mad(-l41, x4, N::mad(-l31, x3, N::mad(-l21, x2, b1 * r1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -241,9 +235,20 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     // ln(p/W) (natural or base-2 logs, see Num::LOG_SCALE) and q_a = W_a / p_a
     T L[9], q[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        L[a] = N::lnp(del[a], y[a]);
-        q[a] = N::rcp(y[a]);
+    for (int a = 0; a < 9; ++a) L[a] = N::lnp(del[a], y[a]);
+    if constexpr (!std::is_same<T, double>::value) {
+        // FP32: opposite populations share one reciprocal of their product
+        // (5 reciprocals instead of 9, each result within ~2 ulp)
+        const T p13 = y[1] * y[3], p24 = y[2] * y[4], p57 = y[5] * y[7], p68 = y[6] * y[8];
+        const T r13 = N::rcp(p13), r24 = N::rcp(p24), r57 = N::rcp(p57), r68 = N::rcp(p68);
+        q[0] = N::rcp(y[0]);
+        q[1] = y[3] * r13; q[3] = y[1] * r13;
+        q[2] = y[4] * r24; q[4] = y[2] * r24;
+        q[5] = y[7] * r57; q[7] = y[5] * r57;
+        q[6] = y[8] * r68; q[8] = y[6] * r68;
+    } else {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) q[a] = N::rcp(y[a]);
     }
     // A/9 with 1/p_a = q_a / W_a: rest 9/4 q, axis 9 q, diagonal 36 q.
     const T p13 = q[1] + q[3], p24 = q[2] + q[4];

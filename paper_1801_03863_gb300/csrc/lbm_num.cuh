@@ -6,8 +6,12 @@
 //   F2      FP32 path, two nodes per value: the packed FP32x2 instructions of
 //           sm_100+ (__fadd2_rn, __fmul2_rn, __ffma2_rn) do both nodes in one
 //           issue; reciprocals and logarithms run per lane on the MUFU unit.
-// Every operation is rounded like its scalar FP32 counterpart, so F2 and
-// float give bitwise identical results.
+//   F1      FP32, one node per value (the one-off in-place collision).
+// The compiler may fuse a packed product whose only use is a following
+// packed add into one packed FMA (it does so even for the _rn forms), which
+// scalar __fmul_rn / __fadd_rn never are; so F1 and F2 agree to FP32
+// rounding, not bit for bit.  All step kernels use F2 with the same
+// collision code and agree bit for bit with each other.
 //
 // FP32 transcendental choice: ln(p/W) is needed as log(1 + delta) with
 // |delta| < 1 typically; the FP32 path evaluates log2(1 + delta) with the
@@ -46,10 +50,9 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b) {
 }
 __device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
 
-// Scalar FP32 with the same rounding discipline as F2: every + - * rounds
-// separately (__fadd_rn / __fmul_rn are never contracted into FMAs), and
-// fused operations are explicit (Num<F1>::mad).  Scalar and packed FP32
-// paths therefore give bitwise identical results.
+// Scalar FP32: every + - * rounds separately (__fadd_rn / __fmul_rn are
+// never contracted into FMAs) and fused operations are explicit
+// (Num<F1>::mad).
 struct F1 {
     float v;
     F1() = default;

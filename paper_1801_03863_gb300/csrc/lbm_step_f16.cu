@@ -11,11 +11,9 @@ const void* step_kernel_f16(int lattice, int collision, int V) {
     return nullptr;
 }
 
-const void* step_kernel_smem_f16(int collision, int P, int variant, size_t* smem_bytes) {
-    if (variant == 1)  // small tiles: node pairs only
-        return P == 2 ? pick_step_kernel_smem<__half, 2, 1>(collision, smem_bytes) : nullptr;
-    return P == 1 ? pick_step_kernel_smem<__half, 1, 0>(collision, smem_bytes)
-                  : pick_step_kernel_smem<__half, 2, 0>(collision, smem_bytes);
+const void* step_kernel_smem_f16(int collision, int variant, size_t* smem_bytes) {
+    return variant == 1 ? pick_step_kernel_smem<__half, 1>(collision, smem_bytes)
+                        : pick_step_kernel_smem<__half, 0>(collision, smem_bytes);
 }
 
 }  // namespace lbm

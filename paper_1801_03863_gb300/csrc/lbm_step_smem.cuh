@@ -148,18 +148,6 @@ __device__ __forceinline__ float2 smem_pair(const S* row, int wb) {
     }
 }
 
-// Single node x of one plane (one-node-per-thread variant): element e - VX.
-template <typename S, int VX>
-__device__ __forceinline__ float smem_elem(const S* row, int e) {
-    return to_compute<float, S>(row[e - VX]);
-}
-
-// Store one node.
-template <typename S>
-__device__ __forceinline__ void store_elem(S* p, float a) {
-    *p = Store<S>::from(a);
-}
-
 // Store one pair.
 template <typename S>
 __device__ __forceinline__ void store_pair(S* p, float a, float b) {
@@ -172,32 +160,19 @@ __device__ __forceinline__ void store_pair(S* p, float a, float b) {
     }
 }
 
-// The nine pulled values of one consumer unit (a node pair, P = 2, or a
-// single node, P = 1) from the stage rows of the current tile row.
-template <typename S, int P, typename CT>
-__device__ __forceinline__ void load_unit(const S* srow, int wb, int plane_elems, CT (&d)[9]) {
-    if constexpr (P == 2) {
-        d[0] = F2(smem_pair<S, 0>(srow + 0 * plane_elems, wb));
-        d[1] = F2(smem_pair<S, 1>(srow + 1 * plane_elems, wb));
-        d[2] = F2(smem_pair<S, 0>(srow + 2 * plane_elems, wb));
-        d[3] = F2(smem_pair<S, -1>(srow + 3 * plane_elems, wb));
-        d[4] = F2(smem_pair<S, 0>(srow + 4 * plane_elems, wb));
-        d[5] = F2(smem_pair<S, 1>(srow + 5 * plane_elems, wb));
-        d[6] = F2(smem_pair<S, -1>(srow + 6 * plane_elems, wb));
-        d[7] = F2(smem_pair<S, -1>(srow + 7 * plane_elems, wb));
-        d[8] = F2(smem_pair<S, 1>(srow + 8 * plane_elems, wb));
-    } else {
-        static_assert(std::is_same<CT, F1>::value, "single nodes use F1");
-        d[0] = smem_elem<S, 0>(srow + 0 * plane_elems, wb);
-        d[1] = smem_elem<S, 1>(srow + 1 * plane_elems, wb);
-        d[2] = smem_elem<S, 0>(srow + 2 * plane_elems, wb);
-        d[3] = smem_elem<S, -1>(srow + 3 * plane_elems, wb);
-        d[4] = smem_elem<S, 0>(srow + 4 * plane_elems, wb);
-        d[5] = smem_elem<S, 1>(srow + 5 * plane_elems, wb);
-        d[6] = smem_elem<S, -1>(srow + 6 * plane_elems, wb);
-        d[7] = smem_elem<S, -1>(srow + 7 * plane_elems, wb);
-        d[8] = smem_elem<S, 1>(srow + 8 * plane_elems, wb);
-    }
+// The nine pulled values of one node pair from the stage rows of the
+// current tile row.
+template <typename S>
+__device__ __forceinline__ void load_unit(const S* srow, int wb, int plane_elems, F2 (&d)[9]) {
+    d[0] = F2(smem_pair<S, 0>(srow + 0 * plane_elems, wb));
+    d[1] = F2(smem_pair<S, 1>(srow + 1 * plane_elems, wb));
+    d[2] = F2(smem_pair<S, 0>(srow + 2 * plane_elems, wb));
+    d[3] = F2(smem_pair<S, -1>(srow + 3 * plane_elems, wb));
+    d[4] = F2(smem_pair<S, 0>(srow + 4 * plane_elems, wb));
+    d[5] = F2(smem_pair<S, 1>(srow + 5 * plane_elems, wb));
+    d[6] = F2(smem_pair<S, -1>(srow + 6 * plane_elems, wb));
+    d[7] = F2(smem_pair<S, -1>(srow + 7 * plane_elems, wb));
+    d[8] = F2(smem_pair<S, 1>(srow + 8 * plane_elems, wb));
 }
 
 __device__ __forceinline__ int wrap_index(int v, int n) {
@@ -229,20 +204,20 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
 #define LBM_SMEM_MINBLOCKS 2  // resident CTAs per SM the register budget aims at
 #endif
 
-#ifndef LBM_SMEM_MINBLOCKS1
-#define LBM_SMEM_MINBLOCKS1 2  // resident CTAs per SM, one-node-per-thread variant
-#endif
-
-// P = nodes per thread and row: 2 (node pairs, packed FP32x2 arithmetic) or
-// 1 (single nodes, scalar FP32, fewer registers and more resident warps).
-template <typename S, int COLL, int TILE, int NST, int P>
-__global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MINBLOCKS1)
+// Every thread collides node pairs (P = 2 nodes per unit) in packed FP32x2
+// arithmetic.  All step kernels run the same packed collision code, so their
+// results agree bit for bit: the compiler may fuse a packed product into a
+// following packed add, and it does so alike wherever the collision is
+// inlined, which scalar code would not reproduce.
+template <typename S, int COLL, int TILE, int NST>
+__global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     step_kernel_smem(const StepArgs args) {
     using TS = SmemTile<S, TILE, NST>;
     constexpr int E = TS::E;
     constexpr int Q = 9;
     constexpr int NS = TS::STAGES;
-    using CT = typename std::conditional<P == 2, F2, F1>::type;
+    constexpr int P = 2;
+    using CT = F2;
     using N = Num<CT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations must be 16-byte (here: 128-byte) aligned: round the
@@ -327,17 +302,17 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
         const int64_t pitch = p.pitch, plane = p.plane, off = p.off;
         S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
 
-        const int cl2 = p.xl2 - (P == 2 ? 1 : 0);  // log2 of the thread columns per row
+        const int cl2 = p.xl2 - 1;  // log2 of the thread columns per row
         const int px = tid & ((1 << cl2) - 1);
         const int rg = tid >> cl2;                  // first row of this thread
         const int rstep = TS::THREADS >> cl2;       // rows between this thread's units
         const int x = x0 + P * px;
         // own position in a shared row: element E + P px (in words for pairs
         // of 2-byte types)
-        const int wb = (P == 1) ? (E + px) : ((sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px));
+        const int wb = (sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px);
         const Rates<CT> rates{CT(p.omega), CT(p.omega2), CT(p.s_e), CT(p.s_eps)};
         uint32_t n_skip = 0, n_unst = 0;
-        const bool second = (P == 2) && (x + 1 < nx);
+        const bool second = x + 1 < nx;
         const bool xedge = (x == 0) || (x + P - 1 >= nx - 1);
         const bool xin = x < nx;
         constexpr int MAXP = TS::TILE_NODES / (P * TS::THREADS);  // units per thread
@@ -364,7 +339,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
             CT d[Q];
             {
                 const S* srow = sbase + r * SP;
-                load_unit<S, P>(srow, wb, TS::PLANE_ELEMS, d);
+                load_unit<S>(srow, wb, TS::PLANE_ELEMS, d);
             }
             if (y >= ny || !xin) continue;
             // node (pair) on the lattice's outer ring: boundary rules apply
@@ -375,8 +350,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                 for (int a = 0; a < Q; ++a) {
                     const float2 g = global_pair<S>(gb + a * plane, pitch, nx, ny, bc, x, y,
                                                     D2Q9::vx(a), D2Q9::vy(a));
-                    if constexpr (P == 2) d[a] = F2(g);
-                    else d[a] = F1(g.x);
+                    d[a] = F2(g);
                 }
             }
             CT o[Q];
@@ -393,7 +367,7 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                         // collision (the stage is released after the tile)
                         const S* srow = sbase + r * SP;
                         CT v[Q];
-                        load_unit<S, P>(srow, wb, TS::PLANE_ELEMS, v);
+                        load_unit<S>(srow, wb, TS::PLANE_ELEMS, v);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) N::set_lane(o[a], l, N::lane(v[D2Q9::opp(a)], l));
                         sts &= ~(3u << (2 * l));
@@ -409,24 +383,16 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
                 n_skip += __popc(sts & (ST_NEWTON_SKIPPED * 5u));
                 n_unst += __popc(sts & (ST_UNSTABLE * 5u));
             }
-            if constexpr (P == 1) {
+            // the second node of a pair beyond the row (odd widths) is row
+            // padding: keep it zero
+            if (!second) {
 #pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    store_elem<S>(op, o[a].v);
-                    op += plane;
-                }
-            } else {
-                // the second node of a pair beyond the row (odd widths) is
-                // row padding: keep it zero
-                if (!second) {
+                for (int a = 0; a < Q; ++a) o[a].v.y = 0.f;
+            }
 #pragma unroll
-                    for (int a = 0; a < Q; ++a) o[a].v.y = 0.f;
-                }
-#pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    store_pair<S>(op, o[a].v.x, o[a].v.y);
-                    op += plane;
-                }
+            for (int a = 0; a < Q; ++a) {
+                store_pair<S>(op, o[a].v.x, o[a].v.y);
+                op += plane;
             }
         }
         __syncwarp();
@@ -447,10 +413,10 @@ __global__ void __launch_bounds__(256, P == 2 ? LBM_SMEM_MINBLOCKS : LBM_SMEM_MI
     }
 }
 
-// The TMA-staged D2Q9 kernel for a collision rule, P nodes per unit and
-// tile geometry VARIANT (0: large tiles, 1: small tiles, see
-// smem_tile_nodes); *smem_bytes receives its dynamic shared memory size.
-template <typename S, int P, int VARIANT>
+// The TMA-staged D2Q9 kernel for a collision rule and tile geometry VARIANT
+// (0: large tiles, 1: small tiles, see smem_tile_nodes); *smem_bytes
+// receives its dynamic shared memory size.
+template <typename S, int VARIANT>
 const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
     constexpr int TN = VARIANT == 0 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4)
                                     : (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL);
@@ -458,11 +424,11 @@ const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
     using TS = SmemTile<S, TN, NS>;
     *smem_bytes = TS::SMEM_BYTES;
     switch (collision) {
-        case COLL_MINXENT4: return (const void*)&step_kernel_smem<S, COLL_MINXENT4, TN, NS, P>;
-        case COLL_SRT: return (const void*)&step_kernel_smem<S, COLL_SRT, TN, NS, P>;
-        case COLL_MINXENT2: return (const void*)&step_kernel_smem<S, COLL_MINXENT2, TN, NS, P>;
+        case COLL_MINXENT4: return (const void*)&step_kernel_smem<S, COLL_MINXENT4, TN, NS>;
+        case COLL_SRT: return (const void*)&step_kernel_smem<S, COLL_SRT, TN, NS>;
+        case COLL_MINXENT2: return (const void*)&step_kernel_smem<S, COLL_MINXENT2, TN, NS>;
         case COLL_MRT:
-        case COLL_TRT: return (const void*)&step_kernel_smem<S, COLL_MRT, TN, NS, P>;
+        case COLL_TRT: return (const void*)&step_kernel_smem<S, COLL_MRT, TN, NS>;
     }
     return nullptr;
 }
