@@ -234,12 +234,20 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
 
     // ln(p/W) (natural or base-2 logs, see Num::LOG_SCALE) and q_a = W_a / p_a
     T L[9], q[9];
+    // FP32 MinxEnt2 needs only the energy-row gradient (b_e, b_p): it takes
+    // the logarithms of y_0 and of the axis and diagonal products (3 MUFU
+    // operations instead of 9); MinxEnt4 keeps one logarithm per population,
+    // which measured faster there.
+    constexpr bool LOGP = !std::is_same<T, double>::value && NFREE == 2;
+    if constexpr (!LOGP) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) L[a] = N::lnp(del[a], y[a]);
+        for (int a = 0; a < 9; ++a) L[a] = N::lnp(del[a], y[a]);
+    }
+    T p13 = T(0.0), p24 = T(0.0), p57 = T(0.0), p68 = T(0.0);
     if constexpr (!std::is_same<T, double>::value) {
         // FP32: opposite populations share one reciprocal of their product
         // (5 reciprocals instead of 9, each result within ~2 ulp)
-        const T p13 = y[1] * y[3], p24 = y[2] * y[4], p57 = y[5] * y[7], p68 = y[6] * y[8];
+        p13 = y[1] * y[3]; p24 = y[2] * y[4]; p57 = y[5] * y[7]; p68 = y[6] * y[8];
         const T r13 = N::rcp(p13), r24 = N::rcp(p24), r57 = N::rcp(p57), r68 = N::rcp(p68);
         q[0] = N::rcp(y[0]);
         q[1] = y[3] * r13; q[3] = y[1] * r13;
@@ -251,29 +259,37 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         for (int a = 0; a < 9; ++a) q[a] = N::rcp(y[a]);
     }
     // A/9 with 1/p_a = q_a / W_a: rest 9/4 q, axis 9 q, diagonal 36 q.
-    const T p13 = q[1] + q[3], p24 = q[2] + q[4];
+    const T e13 = q[1] + q[3], e24 = q[2] + q[4];
     const T d13 = q[1] - q[3], d24 = q[2] - q[4];
     const T s57 = q[5] + q[7], s68 = q[6] + q[8];
     const T d57 = q[5] - q[7], d68 = q[6] - q[8];
-    const T Qa = p13 + p24;
+    const T Qa = e13 + e24;
     const T qd = s57 + s68;
     const T dx = d57 - d68, dy = d57 + d68;
     // rows of T used: e (M2), eps (M3), q_x (M5), q_y (M7)
     const T A_ee = N::mad(T(16.0), qd, N::mad(T(4.0), q[0], Qa));
     const T A_ep = N::mad(T(8.0), qd, N::mad(T(-4.0), q[0], Qa + Qa));
     const T A_pp = T(4.0) * (q[0] + Qa + qd);
-    const T La = (L[1] + L[2]) + (L[3] + L[4]);
-    const T Ld = (L[5] + L[6]) + (L[7] + L[8]);
-    const T b_e = N::mad(T(-4.0), L[0], N::mad(T(2.0), Ld, -La));
-    const T b_p = N::mad(T(4.0), L[0], N::mad(T(-2.0), La, Ld));
+    T L0, La, Ld;
+    if constexpr (LOGP) {
+        L0 = N::lnp(del[0], y[0]);
+        La = N::lnp(T(0.0), p13 * p24);
+        Ld = N::lnp(T(0.0), p57 * p68);
+    } else {
+        L0 = L[0];
+        La = (L[1] + L[2]) + (L[3] + L[4]);
+        Ld = (L[5] + L[6]) + (L[7] + L[8]);
+    }
+    const T b_e = N::mad(T(-4.0), L0, N::mad(T(2.0), Ld, -La));
+    const T b_p = N::mad(T(4.0), L0, N::mad(T(-2.0), La, Ld));
     T se, sps, sx_ = T(0.0), sy_ = T(0.0);
     if constexpr (NFREE == 4) {
         const T A_ex = N::mad(T(8.0), dx, d13 + d13);
         const T A_px = T(4.0) * (d13 + dx);
-        const T A_xx = T(4.0) * (p13 + qd);
+        const T A_xx = T(4.0) * (e13 + qd);
         const T A_ey = N::mad(T(8.0), dy, d24 + d24);
         const T A_py = T(4.0) * (d24 + dy);
-        const T A_yy = T(4.0) * (p24 + qd);
+        const T A_yy = T(4.0) * (e24 + qd);
         const T A_xy = T(4.0) * (s57 - s68);
         const T l57 = L[5] - L[7], l68 = L[6] - L[8];
         const T b_x = N::mad(T(2.0), L[3] - L[1], l57 - l68);
@@ -302,13 +318,25 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         // +0 for finite c and NaN otherwise.
         T chk = (NFREE == 4) ? (se + sps) + (sx_ + sy_) : se + sps;
         chk = chk - chk;
+        // logarithms of products: two negative y can cancel in a product, so
+        // the sign bits of y are tested explicitly
+        uint32_t neg[N::LANES];
 #pragma unroll
-        for (int l = 0; l < N::LANES; ++l) rare = rare || (N::lane(chk, l) != 0.f);
+        for (int l = 0; l < N::LANES; ++l) {
+            neg[l] = 0u;
+            if constexpr (LOGP) {
+#pragma unroll
+                for (int a = 0; a < 9; ++a) neg[l] |= __float_as_uint(N::lane(y[a], l));
+                neg[l] >>= 31;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < N::LANES; ++l) rare = rare || (N::lane(chk, l) != 0.f) || neg[l];
         if (rare) {
             if constexpr (N::LANES == 1) {
-                ok = N::lane(chk, 0) == 0.f;
+                ok = N::lane(chk, 0) == 0.f && !neg[0];
             } else {
-                ok = {N::lane(chk, 0) == 0.f, N::lane(chk, 1) == 0.f};
+                ok = {N::lane(chk, 0) == 0.f && !neg[0], N::lane(chk, 1) == 0.f && !neg[1]};
             }
             se = N::sel(ok, se, T(0.0));
             sps = N::sel(ok, sps, T(0.0));
