@@ -326,11 +326,8 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
         // rows per unit
         S* orow = dst + off + (int64_t)(y0 + rg) * pitch + x;
         const int64_t ostep = (int64_t)rstep * pitch;
-#ifdef LBM_SMEM_INTERLEAVE
-#pragma unroll
-#else
+        // one unit at a time (unrolling raises register pressure and measured slower)
 #pragma unroll 1
-#endif
         for (int k = 0; k < MAXP; ++k) {
             const int r = rg + k * rstep;
             const int y = y0 + r;
