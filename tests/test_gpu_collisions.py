@@ -236,3 +236,44 @@ def test_reduced_precision_one_step_every_node(rule, storage):
     u = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}[storage]
     tol = u * np.abs(fo - w) * 1.01 + 2e-6 * w
     assert np.all(np.abs(f - fo) <= tol), np.max(np.abs(f - fo) - tol)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("rule", ["minxent4", "minxent2"])
+def test_negative_start_pair_skips_newton(rule, storage):
+    """Reading C-NEG when two opposite start probabilities are negative
+    together: a uniform state at rest with a strongly negative xx-stress and
+    tau = 300.5 has y_1 = y_3 ~ -0.2 (all other y positive) for several steps.
+    Their product is positive, so a gradient formed from logarithms of
+    products (the FP32 MinxEnt2 path) only sees the sign through its
+    explicit sign-bit test.  Every node must skip its Newton step and keep
+    p^start (which has negative populations, so it also counts as unstable),
+    exactly as the oracle does."""
+    W9_ = W9
+    dev = np.array([0, -1, 2, -1, 2, 0, 0, 0, 0.0])
+    nx, ny, nu, steps = 24, 10, 100.0, 5
+    f0 = np.repeat(W9_ * (1 + dev), nx * ny).reshape(9, ny, nx)
+    compute = "f64" if storage == "f64" else "f32"
+    with lbm.Lattice("d2q9", [(nx, ny)], nu, "periodic", compute=compute, storage=storage,
+                     collision=rule) as lat:
+        lat.set_populations(f0)
+        lat.step(steps)
+        f = lat.populations().reshape(9, ny, nx)
+        st = lat.status()
+    sim = oracle.Sim(oracle.D2Q9, nx, ny, oracle.tau_from_nu(nu), oracle.BC_PERIODIC,
+                     collision=_orc_coll(rule))
+    sim.set_f(f0)
+    sim.step(steps)
+    co = sim.counters()
+    assert co["newton_skipped"] == nx * ny * steps
+    assert st["newton_skipped"] == co["newton_skipped"], (st, co)
+    assert st["unstable"] == co["unstable"], (st, co)
+    fo = sim.get_f()
+    if storage == "f64":
+        assert _rel(f, fo) <= TOL64
+    else:
+        u = {"f32": 2.0 ** -24, "f16": 2.0 ** -11}[storage]
+        w = W9_[:, None, None]
+        # a few FP32 steps on O(1) values plus the storage rounding of each deviation
+        tol = steps * (u * np.abs(fo - w) * 1.01 + 4e-7 * w)
+        assert np.all(np.abs(f - fo) <= tol), np.max(np.abs(f - fo) - tol)
