@@ -73,8 +73,9 @@ int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const 
     int64_t n = 0;
     if (s.kind >= 1) {
         for (auto& d : dims) {
-            const int64_t X = smem_tile_width(d.first);
-            const int64_t R = smem_tile_nodes(storage, s.kind - 1) / X;
+            const int tn = smem_tile_nodes(storage, s.kind - 1);
+            const int64_t X = smem_tile_width(d.first, tn);
+            const int64_t R = tn / X;
             n += ((d.first + X - 1) / X) * ((d.second + R - 1) / R);
         }
         return n;
@@ -150,8 +151,8 @@ Carve carve(const Layout& L, int lattice, int storage, int count) {
     p += al(sizeof(double) * 3 * (size_t)CONS_PARTIALS * count);
     c.stage_off = p;
     p += al(sizeof(double) * std::max<int64_t>(3 * L.total_nodes, Q * L.total_nodes));
-    c.tmap_off = p;  // two TMA tensor maps (one per population buffer) per instance
-    p += al(2 * sizeof(CUtensorMapOpaque) * count);
+    c.tmap_off = p;  // four TMA tensor maps per instance: [buffer][tile | halo]
+    p += al(4 * sizeof(CUtensorMapOpaque) * count);
     c.err_off = p;
     p += 256;
     c.total = p;
@@ -178,7 +179,7 @@ struct lbm_ctx {
     unsigned long long* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_stage = nullptr;
-    CUtensorMapOpaque* d_tmaps = nullptr;  // [buffer][instance]
+    CUtensorMapOpaque* d_tmaps = nullptr;  // [buffer][tile | halo][instance]
     unsigned int* d_error = nullptr;
     int tmaps_variant = -1;  // tile variant the TMA tensor maps were built for
     std::vector<TileDesc> tiles;
@@ -238,8 +239,9 @@ std::vector<TileDesc> build_tiles(const lbm_ctx* ctx, const Shape& s) {
     if (s.kind >= 1) {
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
-            const int X = smem_tile_width(in.nx);
-            const int R = smem_tile_nodes(ctx->storage, s.kind - 1) / X;
+            const int tn = smem_tile_nodes(ctx->storage, s.kind - 1);
+            const int X = smem_tile_width(in.nx, tn);
+            const int R = tn / X;
             for (int64_t y0 = 0; y0 < in.ny; y0 += R)
                 for (int64_t x0 = 0; x0 < in.nx; x0 += X)
                     t.push_back({(int32_t)i, (int32_t)x0, (int32_t)y0, (int32_t)X});
@@ -315,9 +317,11 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     return LBM_OK;
 }
 
-// TMA tensor maps of both population buffers: per instance a 4-D view
-// (element within a 16-byte chunk, chunk, row, plane) with a box of one
-// tile of the staged kernel plus a one-chunk halo on each side in x.
+// TMA tensor maps of both population buffers: per instance a 3-D view
+// (x < nx, row, plane) of the populations, once with the box of one plane
+// of a tile of the staged kernel (loads and stores: x beyond nx reads as
+// zero and is not written) and once with a 16-byte-wide box of the tile's
+// rows (the x halo loads).
 int build_tensor_maps(lbm_ctx* ctx, int variant) {
     if (ctx->tmaps_variant == variant) return LBM_OK;
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -333,19 +337,21 @@ int build_tensor_maps(lbm_ctx* ctx, int variant) {
     const size_t es = dtype_bytes(ctx->storage);
     const int E = (int)(16 / es);
     const int tile_nodes = smem_tile_nodes(ctx->storage, variant);
-    std::vector<CUtensorMap> maps(2 * (size_t)ctx->count);
-    for (int b = 0; b < 2; ++b) {
+    std::vector<CUtensorMap> maps(4 * (size_t)ctx->count);
+    for (int m = 0; m < 4; ++m) {
+        const int b = m >> 1;
+        const bool halo = (m & 1) != 0;
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
-            const int X = smem_tile_width(in.nx), R = tile_nodes / X;
+            const int X = smem_tile_width(in.nx, tile_nodes), R = tile_nodes / X;
             void* base = ctx->buf[b] + (size_t)in.off * es;
-            cuuint64_t dims[4] = {(cuuint64_t)E, (cuuint64_t)(in.pitch / E), (cuuint64_t)in.ny, 9};
-            cuuint64_t strides[3] = {16, (cuuint64_t)in.pitch * es, (cuuint64_t)in.plane * es};
-            cuuint32_t box[4] = {(cuuint32_t)E, (cuuint32_t)(X / E + 2), (cuuint32_t)R, 1};
-            cuuint32_t estr[4] = {1, 1, 1, 1};
-            CUresult r = encode(&maps[(size_t)b * ctx->count + i],
+            cuuint64_t dims[3] = {(cuuint64_t)in.nx, (cuuint64_t)in.ny, 9};
+            cuuint64_t strides[2] = {(cuuint64_t)in.pitch * es, (cuuint64_t)in.plane * es};
+            cuuint32_t box[3] = {(cuuint32_t)(halo ? E : X), (cuuint32_t)R, 1};
+            cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = encode(&maps[(size_t)m * ctx->count + i],
                                 es == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) {
@@ -374,7 +380,9 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
     a.th = ctx->shape.th;
     a.rho0 = ctx->rho0;
     a.status = ctx->d_status;
-    a.tmaps = ctx->d_tmaps + (size_t)src * ctx->count;
+    a.tmaps = ctx->d_tmaps + (size_t)src * 2 * ctx->count;
+    a.tmaps_halo = ctx->d_tmaps + (size_t)(src * 2 + 1) * ctx->count;
+    a.tmaps_dst = ctx->d_tmaps + (size_t)(1 - src) * 2 * ctx->count;
     a.error = ctx->d_error;
     return a;
 }

@@ -74,6 +74,12 @@ inline int smem_tile_nodes(int storage, int variant) {
     if (variant == 1) return storage == 1 ? LBM_SMEM_TILE4_SMALL : LBM_SMEM_TILE2_SMALL;
     return storage == 1 ? LBM_SMEM_TILE4 : LBM_SMEM_TILE2;
 }
-inline int smem_tile_width(int64_t nx) { return nx >= 256 ? 256 : (nx >= 128 ? 128 : 64); }
+// Tile width: 64, 128 or 256 nodes by the instance width, at most
+// tile_nodes / 8, so that each warp's units (tile_nodes / 512 rows of 64
+// nodes) cover whole tile rows.
+inline int smem_tile_width(int64_t nx, int tile_nodes) {
+    const int w = nx >= 256 ? 256 : (nx >= 128 ? 128 : 64);
+    return w < tile_nodes / 8 ? w : tile_nodes / 8;
+}
 
 }  // namespace lbm

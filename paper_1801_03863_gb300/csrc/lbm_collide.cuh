@@ -124,6 +124,27 @@ __device__ __forceinline__ uint32_t sign_status(const T (&out)[Q], const double 
     return st;
 }
 
+// The stability criterion (finite, non-negative populations) for rules
+// without a Newton step: the FP64 path compares every population, the FP32
+// paths test the sign bits of f^post and that the sum of the deviations is
+// finite (a NaN or infinite population makes it so).
+template <typename T, int Q>
+__device__ __forceinline__ uint32_t plain_status(const T (&out)[Q], const double (&w)[Q], T rho0) {
+    using N = Num<T>;
+    if constexpr (std::is_same<T, double>::value) {
+        return lane_status<T>(true, finite_nonneg<T, Q>(out, w, rho0));
+    } else {
+        uint32_t st = sign_status<T, Q>(out, w, rho0);
+        T s = out[0];
+#pragma unroll
+        for (int a = 1; a < Q; ++a) s = s + out[a];
+#pragma unroll
+        for (int l = 0; l < N::LANES; ++l)
+            if (!(fabsf(N::lane(s, l)) < 1e30f)) st |= ST_UNSTABLE << (2 * l);
+        return st;
+    }
+}
+
 // 4x4 symmetric positive definite solve A x = b by an LDL^T factorisation:
 // A = L D L^T with unit lower-triangular L, then L z = b, x = L^-T D^-1 z.
 // Four reciprocals (of the pivots) and 32 multiply-adds; A is given as its
@@ -421,10 +442,7 @@ __device__ __forceinline__ uint32_t srt_d2q9(const T (&d)[9], T rho0, const Rate
         const T deq = N::mad(wa * rho, xi[a], wa * drho);
         out[a] = N::mad(omega, deq - d[a], d[a]);
     }
-    typename N::Pred all;
-    if constexpr (N::LANES == 1) all = true;
-    else all = {true, true};
-    return lane_status<T>(all, finite_nonneg<T, 9>(out, W, rho0));
+    return plain_status<T, 9>(out, W, rho0);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,10 +503,7 @@ __device__ __forceinline__ uint32_t mrt_d2q9(const T (&d)[9], T rho0, const Rate
     out[7] = d[7] + (gp - xp);
     out[6] = d[6] + (gm - xm);
     out[8] = d[8] + (gm + xm);
-    typename N::Pred all;
-    if constexpr (N::LANES == 1) all = true;
-    else all = {true, true};
-    return lane_status<T>(all, finite_nonneg<T, 9>(out, W, rho0));
+    return plain_status<T, 9>(out, W, rho0);
 }
 
 // ---------------------------------------------------------------------------
@@ -514,10 +529,7 @@ __device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, const Rate
     out[0] = N::mad(omega, deq0 - d[0], d[0]);
     out[1] = N::mad(omega, deq1 - d[1], d[1]);
     out[2] = N::mad(omega, deq2 - d[2], d[2]);
-    typename N::Pred all;
-    if constexpr (N::LANES == 1) all = true;
-    else all = {true, true};
-    return lane_status<T>(all, finite_nonneg<T, 3>(out, W, rho0));
+    return plain_status<T, 3>(out, W, rho0);
 }
 
 // Dispatch by lattice and rule.

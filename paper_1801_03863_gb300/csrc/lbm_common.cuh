@@ -126,7 +126,9 @@ struct StepArgs {
     int32_t th;       // tile height in rows
     double rho0;
     unsigned long long* status;  // [count][2]: newton skipped, unstable
-    const void* tmaps;           // per-instance tensor maps of src (TMA kernel only)
+    const void* tmaps;           // TMA kernel only, per instance: tensor maps of src with
+    const void* tmaps_halo;      // the tile box and with the halo box,
+    const void* tmaps_dst;       // and of dst with the tile box (the stores)
     unsigned int* error;         // device error word (bounded waits that ran out)
 };
 

@@ -1,4 +1,4 @@
-// lbm_step_smem.cuh -- the D2Q9 step with TMA staging of halo tiles
+// lbm_step_smem.cuh -- the D2Q9 step with TMA staging of tiles in and out
 // (FP32 collide arithmetic, FP32 / FP16 / BF16 storage).
 //
 // Same time step as step_kernel (pull-stream + collide + boundary rules of
@@ -11,25 +11,35 @@
 //    of arithmetic-bound rules, and small tiles (1024 / 512) with a
 //    three-stage ring, which keep more copies in flight for bandwidth-bound
 //    ones; the autotuner picks per context.
-//  * Each instance's populations are described to TMA as a 4-D tensor
-//    (element within a 16-byte chunk, chunk, row, plane).  For every plane
-//    one elected thread issues a single tensor copy of the tile's rows
-//    shifted by -v_y, one chunk wider on each side in x (the halo); copies
-//    outside the lattice are zero-filled by the hardware, which is exactly
-//    the cavity's "outside" value (deviation 0).
+//  * Each instance's populations are described to TMA as a 3-D tensor
+//    (x < nx, row, plane).  Every copy starts at an x that is a multiple of
+//    16 bytes (tiles start at multiples of 64 nodes, halo chunks 16 bytes
+//    beside them), as tensor copies require.  For every plane
+//    one elected thread issues a tensor copy of the tile's rows shifted by
+//    -v_y into a dense R x X block of the stage, and for the six planes with
+//    v_x != 0 one more copy of the 16-byte chunk beside the tile on the side
+//    the pull comes from (the halo column).  Copies outside the lattice are
+//    zero-filled by the hardware, which is exactly the cavity's "outside"
+//    value (deviation 0).
 //  * A ring of STAGES shared-memory stages, each with a "full" mbarrier (the
 //    copies landed) and an "empty" one (every warp is done with it): the
-//    copies of the next tiles are in flight while one is collided.  Every
-//    wait is bounded; on timeout the kernel records an error word and the
-//    CTA leaves after a bounded wait for its own copies still in flight.
+//    copies of the next tiles are in flight while one is collided.
+//  * Each warp owns whole rows of the tile and takes them in units of 32
+//    node pairs (one pair per lane, packed FP32x2 arithmetic), left to right.
+//    A unit writes its post-collision pairs back over its own positions in
+//    the stage once every lane has read them; the one value a later unit
+//    still needs from an overwritten position (the pair left of the next
+//    unit's first node) is parked beforehand in the unused words of the
+//    halo chunk.  When every warp is done with a tile, the elected thread
+//    writes the stage's nine planes out with one tensor store each (rows
+//    and chunks beyond the lattice are clipped by the hardware) and waits
+//    for TMA to have read them before the stage is refilled.
+//  * Every mbarrier wait is bounded; on timeout the kernel records an error
+//    word and the CTA leaves after a bounded wait for its own copies still
+//    in flight.
 //  * Nodes whose pull crosses a periodic or zero-gradient edge, which a zero
 //    fill cannot express, read their neighbours from global memory with the
 //    boundary rule.
-//  * Each thread collides one node pair (packed FP32x2 arithmetic) or one
-//    node per unit, reading 4-byte words from shared memory (consecutive
-//    threads, consecutive words: no bank conflicts) and storing each plane's
-//    pair with one 4- or 8-byte store (a warp writes 128 or 256 contiguous
-//    bytes).
 #pragma once
 #include "lbm_aux.h"
 #include "lbm_collide.cuh"
@@ -52,10 +62,16 @@ struct SmemTile {
     static constexpr int STAGES = NST;             // depth of the shared-memory ring
     static constexpr int THREADS = 256;
     static constexpr int WARPS = THREADS / 32;
+    // units (32 node pairs = 64 nodes of one row) per warp; a warp's units
+    // cover whole rows for X <= 64 * UNITS (smem_tile_width keeps to that)
+    static constexpr int UNITS = TILE_NODES / (2 * THREADS);
     static constexpr int MAX_ROWS = TILE_NODES / 64;  // R at X = 64
-    // elements of one plane at the largest smem footprint (X = 64); a
-    // multiple of 64 elements, so every plane region is 128-byte aligned
-    static constexpr int PLANE_ELEMS = TILE_NODES + 2 * E * MAX_ROWS;
+    // one plane: the dense R x X tile, then its halo column (one 16-byte
+    // chunk per row, room for MAX_ROWS rows)
+    static constexpr int HALO_ELEMS = MAX_ROWS * E;
+    static constexpr int PLANE_ELEMS = TILE_NODES + HALO_ELEMS;
+    static constexpr int PLANE_BYTES = PLANE_ELEMS * (int)sizeof(S);
+    static constexpr int HALO_OFF = TILE_NODES * (int)sizeof(S);  // bytes into a plane
     static constexpr int STAGE_ELEMS = 9 * PLANE_ELEMS;
     static constexpr size_t STAGES_BYTES = (size_t)STAGES * STAGE_ELEMS * sizeof(S);
     // + room to round the dynamic base up to 128 bytes, per-stage tile
@@ -63,7 +79,9 @@ struct SmemTile {
     static constexpr size_t PARAMS_OFF = STAGES_BYTES;
     static constexpr size_t BARS_OFF = PARAMS_OFF + 128 * STAGES;
     static constexpr size_t SMEM_BYTES = 128 + BARS_OFF + 16 * STAGES;
-    static_assert((PLANE_ELEMS * sizeof(S)) % 128 == 0, "plane regions must stay 128-byte aligned");
+    static_assert(UNITS >= 1 && UNITS <= 4, "a unit's halo chunk parks at most 3 values");
+    static_assert(HALO_OFF % 128 == 0 && PLANE_BYTES % 128 == 0,
+                  "tile blocks and halo columns must stay 128-byte aligned");
 };
 
 // Parameters of the tile held by one stage, written by the producing thread
@@ -116,41 +134,104 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2,
-                                            int c3, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                            uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int c0, int c1,
+                                             int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group"
+        " [%0, {%1, %2, %3}], [%4];\n" ::"l"(tmap),
+        "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// the shared-memory sources of every committed store have been read
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// every committed store has been performed
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
 
-// Pair of nodes (2p, 2p+1) of one plane as FP32x2.  `row` points at the
-// shared-memory row of the plane; `wb` is the index (in 32-bit words for
-// 2-byte types, in elements for FP32) of the pair's own position, element
-// E + 2p.  The pull shift -v_x is a compile-time offset from it.
+// Shared-memory byte offsets of one unit, relative to the stage's plane 0:
+//   own  the lane's pair (elements 2p, 2p+1 of its tile row);
+//   lft  the word whose last element is the one left of the pair (2p - 1):
+//        the lane to the left's pair, or for lane 0 a word of the row's halo
+//        chunk (the left halo, or the value parked by the previous unit);
+//   rgt  the word whose first element is the one right of the pair
+//        (2p + 2): the next lane's pair, or for the row's last lane word 0
+//        of the right halo chunk.
+struct UnitOffs {
+    uint32_t own, lft, rgt;
+};
+
+// Pair of nodes (2p, 2p+1) of plane `pl` pulled with shift -VX in x, as
+// FP32x2.
 template <typename S, int VX>
-__device__ __forceinline__ float2 smem_pair(const S* row, int wb) {
+__device__ __forceinline__ float2 smem_pair(const unsigned char* pl, const UnitOffs& u) {
     if constexpr (sizeof(S) == 2) {
-        const uint32_t* w = reinterpret_cast<const uint32_t*>(row) + wb;
+        const uint32_t w0 = *reinterpret_cast<const uint32_t*>(pl + u.own);
         uint32_t v;
-        if constexpr (VX == 0) v = w[0];
-        else if constexpr (VX == 1) v = __byte_perm(w[-1], w[0], 0x5432);  // elements 2p-1, 2p
-        else v = __byte_perm(w[0], w[1], 0x5432);                           // elements 2p+1, 2p+2
+        if constexpr (VX == 0) v = w0;
+        else if constexpr (VX == 1)
+            v = __byte_perm(*reinterpret_cast<const uint32_t*>(pl + u.lft), w0, 0x5432);
+        else
+            v = __byte_perm(w0, *reinterpret_cast<const uint32_t*>(pl + u.rgt), 0x5432);
         if constexpr (std::is_same<S, __half>::value) {
             return __half22float2(*reinterpret_cast<const __half2*>(&v));
         } else {
             return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
         }
     } else {
-        const float* f = reinterpret_cast<const float*>(row) + wb - VX;
-        return make_float2(f[0], f[1]);
+        if constexpr (VX == 0) return *reinterpret_cast<const float2*>(pl + u.own);
+        else if constexpr (VX == 1)
+            return make_float2(*reinterpret_cast<const float*>(pl + u.lft),
+                               *reinterpret_cast<const float*>(pl + u.own));
+        else
+            return make_float2(*reinterpret_cast<const float*>(pl + u.own + 4),
+                               *reinterpret_cast<const float*>(pl + u.rgt));
     }
 }
 
-// Store one pair.
+// The nine pulled values of one node pair.
+template <typename S, int PB>
+__device__ __forceinline__ void load_unit(const unsigned char* st, const UnitOffs& u, F2 (&d)[9]) {
+    d[0] = F2(smem_pair<S, 0>(st + 0 * PB, u));
+    d[1] = F2(smem_pair<S, 1>(st + 1 * PB, u));
+    d[2] = F2(smem_pair<S, 0>(st + 2 * PB, u));
+    d[3] = F2(smem_pair<S, -1>(st + 3 * PB, u));
+    d[4] = F2(smem_pair<S, 0>(st + 4 * PB, u));
+    d[5] = F2(smem_pair<S, 1>(st + 5 * PB, u));
+    d[6] = F2(smem_pair<S, -1>(st + 6 * PB, u));
+    d[7] = F2(smem_pair<S, -1>(st + 7 * PB, u));
+    d[8] = F2(smem_pair<S, 1>(st + 8 * PB, u));
+}
+
+// The word holding the pair's second element (2p + 1) in the planes pulled
+// from x - 1 (1, 5, 8): the value the next unit of the row pulls into its
+// first node.  For 2-byte storage it is the pair's own word, which
+// load_unit has just read.
+template <typename S, int PB>
+__device__ __forceinline__ void park_words(const unsigned char* st, const UnitOffs& u,
+                                           uint32_t (&w)[3]) {
+    const uint32_t at = u.own + (sizeof(S) == 2 ? 0u : 4u);
+    w[0] = *reinterpret_cast<const uint32_t*>(st + 1 * PB + at);
+    w[1] = *reinterpret_cast<const uint32_t*>(st + 5 * PB + at);
+    w[2] = *reinterpret_cast<const uint32_t*>(st + 8 * PB + at);
+}
+
+// Post-collision pair into the stage, over the lane's own position.
 template <typename S>
-__device__ __forceinline__ void store_pair(S* p, float a, float b) {
+__device__ __forceinline__ void smem_store_pair(unsigned char* p, float a, float b) {
     if constexpr (std::is_same<S, __half>::value) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
     } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
@@ -158,21 +239,6 @@ __device__ __forceinline__ void store_pair(S* p, float a, float b) {
     } else {
         *reinterpret_cast<float2*>(p) = make_float2(a, b);
     }
-}
-
-// The nine pulled values of one node pair from the stage rows of the
-// current tile row.
-template <typename S>
-__device__ __forceinline__ void load_unit(const S* srow, int wb, int plane_elems, F2 (&d)[9]) {
-    d[0] = F2(smem_pair<S, 0>(srow + 0 * plane_elems, wb));
-    d[1] = F2(smem_pair<S, 1>(srow + 1 * plane_elems, wb));
-    d[2] = F2(smem_pair<S, 0>(srow + 2 * plane_elems, wb));
-    d[3] = F2(smem_pair<S, -1>(srow + 3 * plane_elems, wb));
-    d[4] = F2(smem_pair<S, 0>(srow + 4 * plane_elems, wb));
-    d[5] = F2(smem_pair<S, 1>(srow + 5 * plane_elems, wb));
-    d[6] = F2(smem_pair<S, -1>(srow + 6 * plane_elems, wb));
-    d[7] = F2(smem_pair<S, -1>(srow + 7 * plane_elems, wb));
-    d[8] = F2(smem_pair<S, 1>(srow + 8 * plane_elems, wb));
 }
 
 __device__ __forceinline__ int wrap_index(int v, int n) {
@@ -217,6 +283,8 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     constexpr int Q = 9;
     constexpr int NS = TS::STAGES;
     constexpr int P = 2;
+    constexpr int PB = TS::PLANE_BYTES;
+    constexpr int ES = (int)sizeof(S);
     using CT = F2;
     using N = Num<CT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -229,9 +297,10 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_al + TS::BARS_OFF);
     uint64_t* empty = full + NS;
     const S* __restrict__ src = static_cast<const S*>(args.src);
-    S* __restrict__ dst = static_cast<S*>(args.dst);
     const CUtensorMapOpaque* tmaps = static_cast<const CUtensorMapOpaque*>(args.tmaps);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const CUtensorMapOpaque* hmaps = static_cast<const CUtensorMapOpaque*>(args.tmaps_halo);
+    const CUtensorMapOpaque* omaps = static_cast<const CUtensorMapOpaque*>(args.tmaps_dst);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const CT rho0v = CT((float)args.rho0);
     const int G = gridDim.x;
     // local tile j of this CTA is global tile blockIdx.x + j * G
@@ -246,101 +315,142 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     }
     __syncthreads();
 
-    // Thread 0 fills stage j % NS with local tile j: parameters, then the
-    // nine plane copies on the stage's full barrier.  Returns false if the
-    // stage was not released in time.
-    auto produce = [&](int j) -> bool {
+    // Thread 0 writes local tile j out of its stage (every warp is done
+    // with it): one tensor store per plane, then a commit.
+    auto store_tile = [&](int j) {
+        const TileDesc tile = args.tiles[blockIdx.x + j * G];
+        const S* sbase = stage_base + (size_t)(j % NS) * TS::STAGE_ELEMS;
+        const void* map = &omaps[tile.inst];
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            tma_store_3d(map, sbase + a * TS::PLANE_ELEMS, tile.cx0, tile.y0, a);
+        bulk_commit();
+    };
+
+    // Thread 0 refills stage j % NS with local tile j in two parts.  First
+    // (release) it waits until every warp is done with the stage's previous
+    // tile j - NS and hands that tile to the tensor stores; returns false
+    // if the stage was not released in time.  Later (fill) it waits until
+    // TMA has read the stores' sources, stores the tile parameters and
+    // issues the plane and halo copies on the stage's full barrier.  In
+    // between, thread 0 collides a unit of its own, so the stores are read
+    // out while it computes.
+    int nstored = 0;  // local tiles handed to TMA stores (thread 0's count)
+    auto release = [&](int j) -> bool {
         const int st = j % NS, fill = j / NS;
-        if (fill > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((fill - 1) & 1))) return false;
+        if (fill == 0) return true;
+        if (!mbar_wait_bounded(&empty[st], (uint32_t)((fill - 1) & 1))) return false;
+        store_tile(j - NS);
+        nstored = j - NS + 1;
+        return true;
+    };
+    auto fill = [&](int j) {
+        const int st = j % NS;
+        bulk_wait_read();
         const TileDesc tile = args.tiles[blockIdx.x + j * G];
         const InstDesc& in = args.inst[tile.inst];
         StageParams& p = params[st];
+        const int X = tile.pad, R = TS::TILE_NODES / X;
         p.off = in.off; p.pitch = in.pitch; p.plane = in.plane;
-        p.inst = tile.inst; p.X = tile.pad; p.x0 = tile.cx0; p.y0 = tile.y0;
-        p.nx = in.nx; p.ny = in.ny; p.bc = in.bc; p.R = TS::TILE_NODES / tile.pad;
-        p.xl2 = 31 - __clz(tile.pad);
+        p.inst = tile.inst; p.X = X; p.x0 = tile.cx0; p.y0 = tile.y0;
+        p.nx = in.nx; p.ny = in.ny; p.bc = in.bc; p.R = R;
+        p.xl2 = 31 - __clz(X);
         p.omega = (float)in.omega;
         p.omega2 = (float)in.omega2;
         p.s_e = (float)in.s_e;
         p.s_eps = (float)in.s_eps;
 #pragma unroll
         for (int a = 0; a < Q; ++a) p.lid[a] = in.lid_dev_f[a];
-        const uint32_t bytes = (uint32_t)(Q * p.R * (p.X + 2 * E) * sizeof(S));
+        const uint32_t bytes = (uint32_t)((Q * R * X + 6 * R * E) * sizeof(S));
         S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
         const void* map = &tmaps[tile.inst];
-        fence_proxy_async_smem();  // consumers' reads of this stage come first
+        const void* hmap = &hmaps[tile.inst];
+        fence_proxy_async_smem();  // consumers' accesses to this stage come first
         mbar_arrive_expect_tx(&full[st], bytes);
 #pragma unroll
         for (int a = 0; a < Q; ++a)
-            tma_load_4d(sbase + a * TS::PLANE_ELEMS, map, 0, tile.cx0 / E - 1,
+            tma_load_3d(sbase + a * TS::PLANE_ELEMS, map, tile.cx0, tile.y0 - D2Q9::vy(a), a,
+                        &full[st]);
+        // halo columns: the chunk left of the tile for the planes pulled
+        // from x - 1, the chunk right of it for those pulled from x + 1
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            if (D2Q9::vx(a) == 0) continue;
+            const int hx = D2Q9::vx(a) == 1 ? tile.cx0 - E : tile.cx0 + X;
+            tma_load_3d(sbase + a * TS::PLANE_ELEMS + TS::TILE_NODES, hmap, hx,
                         tile.y0 - D2Q9::vy(a), a, &full[st]);
-        return true;
+        }
     };
 
     bool fail = false;
-    int issued = 0;  // local tiles handed to TMA (thread 0's count)
+    int issued = 0;  // local tiles handed to TMA loads (thread 0's count)
     int jdone = -1;  // last local tile whose copies this thread saw land
     if (tid == 0) {
-        for (; issued < min(NS - 1, ntl); ++issued)
-            if (!produce(issued)) { fail = true; break; }
+        for (; issued < min(NS - 1, ntl); ++issued) fill(issued);
     }
     for (int j = 0; j < ntl && !fail; ++j) {
         const int st = j % NS;
-        // keep NS - 1 tiles in flight: refill the stage released by tile j - 1
-        if (tid == 0 && issued < ntl && issued == j + NS - 1) {
-            if (produce(issued)) ++issued;
-            else fail = true;
-        }
-        if (!mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1))) fail = true;
+        // keep NS - 1 tiles in flight: the stage released by tile j - 1
+        // takes tile j + NS - 1, filled after this thread's first unit
+        bool refill = tid == 0 && issued < ntl && issued == j + NS - 1;
+        if (refill && !release(issued)) fail = true;
+        if (!fail && !mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1))) fail = true;
         if (fail) break;
         jdone = j;
 
         const StageParams& p = params[st];
         const int X = p.X;
-        const int SP = X + 2 * E;  // smem row length (elements)
         const int x0 = p.x0, y0 = p.y0, nx = p.nx, ny = p.ny, bc = p.bc;
         const int64_t pitch = p.pitch, plane = p.plane, off = p.off;
-        S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
-
-        const int cl2 = p.xl2 - 1;  // log2 of the thread columns per row
-        const int px = tid & ((1 << cl2) - 1);
-        const int rg = tid >> cl2;                  // first row of this thread
-        const int rstep = TS::THREADS >> cl2;       // rows between this thread's units
-        const int x = x0 + P * px;
-        // own position in a shared row: element E + P px (in words for pairs
-        // of 2-byte types)
-        const int wb = (sizeof(S) == 2) ? (E / 2 + px) : (E + 2 * px);
+        unsigned char* sb = reinterpret_cast<unsigned char*>(stage_base + (size_t)st * TS::STAGE_ELEMS);
+        const int sl2 = p.xl2 - 6;         // log2 of the units per tile row
+        const int smask = (1 << sl2) - 1;  // last unit of a row
         const Rates<CT> rates{CT(p.omega), CT(p.omega2), CT(p.s_e), CT(p.s_eps)};
         uint32_t n_skip = 0, n_unst = 0;
-        const bool second = x + 1 < nx;
-        const bool xedge = (x == 0) || (x + P - 1 >= nx - 1);
-        const bool xin = x < nx;
-        constexpr int MAXP = TS::TILE_NODES / (P * TS::THREADS);  // units per thread
         float lid[Q];
         if (bc == BC_CAVITY) {
 #pragma unroll
             for (int a = 0; a < Q; ++a) lid[a] = p.lid[a];
         }
         const int inst = p.inst;
-        // this thread's output position in its first row; advanced by rstep
-        // rows per unit
-        S* orow = dst + off + (int64_t)(y0 + rg) * pitch + x;
-        const int64_t ostep = (int64_t)rstep * pitch;
         // one unit at a time (unrolling raises register pressure and measured slower)
 #pragma unroll 1
-        for (int k = 0; k < MAXP; ++k) {
-            const int r = rg + k * rstep;
+        for (int k = 0; k < TS::UNITS; ++k) {
+            const int u = warp * TS::UNITS + k;
+            const int r = u >> sl2;          // tile row
+            const int sg = u & smask;        // unit within the row
+            const int px = (sg << 5) + lane; // pair within the row
+            const int x = x0 + P * px;
             const int y = y0 + r;
-            S* op = orow;
-            orow += ostep;
+            const uint32_t hrow = (uint32_t)(TS::HALO_OFF + r * 16);  // this row's halo chunk
+            UnitOffs uo;
+            uo.own = (uint32_t)((r * X + P * px) * ES);
+            uo.lft = (lane == 0) ? hrow + 4u * (uint32_t)(3 - sg) : uo.own - 4u;
+            uo.rgt = (lane == 31 && sg == smask) ? hrow : uo.own + (uint32_t)(P * ES);
             CT d[Q];
+            load_unit<S, PB>(sb, uo, d);
+            // The next unit of the row pulls element x - 1 of its first pair
+            // from this unit's last pair, which this unit overwrites: park
+            // the word holding it (planes 1, 5, 8) in the row's halo chunk,
+            // word 3 - (sg + 1) (word 3 holds the left halo itself).
             {
-                const S* srow = sbase + r * SP;
-                load_unit<S>(srow, wb, TS::PLANE_ELEMS, d);
+                uint32_t pw[3];
+                park_words<S, PB>(sb, uo, pw);
+                if (lane == 31 && sg < smask) {
+                    const uint32_t to = hrow + 4u * (uint32_t)(2 - sg);
+                    *reinterpret_cast<uint32_t*>(sb + 1 * PB + to) = pw[0];
+                    *reinterpret_cast<uint32_t*>(sb + 5 * PB + to) = pw[1];
+                    *reinterpret_cast<uint32_t*>(sb + 8 * PB + to) = pw[2];
+                }
             }
-            if (y >= ny || !xin) continue;
+            // Lanes beyond the lattice (x >= nx or y >= ny) collide the
+            // zero-filled or wrapped values they read: their stores are
+            // clipped by TMA and their status is not counted.  So is the
+            // second node of a pair that ends at an odd width.
+            const bool active = (y < ny) && (x < nx);
+            const bool second = x + 1 < nx;
             // node (pair) on the lattice's outer ring: boundary rules apply
-            const bool edge = (y == 0) | (y == ny - 1) | xedge;
+            const bool edge = (y == 0) | (y == ny - 1) | (x == 0) | (x + P - 1 >= nx - 1);
             if (edge && bc != BC_CAVITY) {
                 const S* gb = src + off;
 #pragma unroll
@@ -355,18 +465,19 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
             if (edge && bc == BC_CAVITY) {
 #pragma unroll
                 for (int l = 0; l < P; ++l) {
-                    const int xl2 = x + l;
-                    const bool wall = (xl2 == 0) || (xl2 == nx - 1) || (y == 0);
+                    const int xl = x + l;
+                    const bool wall = (xl == 0) || (xl == nx - 1) || (y == 0);
                     const bool lidn = !wall && (y == ny - 1);
                     if (wall) {
-                        // full-way bounce-back of the pulled populations, re-read
-                        // from the stage so they need not stay live through the
-                        // collision (the stage is released after the tile)
-                        const S* srow = sbase + r * SP;
+                        // full-way bounce-back of the pulled populations,
+                        // re-read from the stage (no lane has written this
+                        // unit's positions yet) so they need not stay live
+                        // through the collision
                         CT v[Q];
-                        load_unit<S>(srow, wb, TS::PLANE_ELEMS, v);
+                        load_unit<S, PB>(sb, uo, v);
 #pragma unroll
-                        for (int a = 0; a < Q; ++a) N::set_lane(o[a], l, N::lane(v[D2Q9::opp(a)], l));
+                        for (int a = 0; a < Q; ++a)
+                            N::set_lane(o[a], l, N::lane(v[D2Q9::opp(a)], l));
                         sts &= ~(3u << (2 * l));
                     } else if (lidn) {
 #pragma unroll
@@ -375,28 +486,38 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
                     }
                 }
             }
-            if (sts) {  // rare: some lane skipped its Newton step or is unstable
+            if (sts && active) {  // rare: some lane skipped its Newton step or is unstable
                 if (!second) sts &= 3u;
                 n_skip += __popc(sts & (ST_NEWTON_SKIPPED * 5u));
                 n_unst += __popc(sts & (ST_UNSTABLE * 5u));
             }
-            // the second node of a pair beyond the row (odd widths) is row
-            // padding: keep it zero
-            if (!second) {
+            __syncwarp();  // every lane has read this unit's positions
 #pragma unroll
-                for (int a = 0; a < Q; ++a) o[a].v.y = 0.f;
-            }
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                store_pair<S>(op, o[a].v.x, o[a].v.y);
-                op += plane;
+            for (int a = 0; a < Q; ++a) smem_store_pair<S>(sb + a * PB + uo.own, o[a].v.x, o[a].v.y);
+            if (refill) {
+                fill(issued);
+                ++issued;
+                refill = false;
             }
         }
+        // this thread's stage writes come before the tensor stores that read them
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
         if (n_skip | n_unst) {
             atomicAdd(args.status + 2 * inst + 0, (unsigned long long)n_skip);
             atomicAdd(args.status + 2 * inst + 1, (unsigned long long)n_unst);
+        }
+    }
+    // thread 0 writes out the tiles whose stages were not refilled
+    if (tid == 0 && !fail) {
+        for (; nstored < ntl; ++nstored) {
+            const int j = nstored;
+            if (!mbar_wait_bounded(&empty[j % NS], (uint32_t)((j / NS) & 1))) {
+                fail = true;
+                break;
+            }
+            store_tile(j);
         }
     }
     if (fail) {
@@ -408,6 +529,7 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
                 mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1));
         }
     }
+    if (tid == 0) bulk_wait_all();  // the stores leave no shared-memory reads behind
 }
 
 // The TMA-staged D2Q9 kernel for a collision rule and tile geometry VARIANT
