@@ -529,7 +529,12 @@ __device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, const Rate
     out[0] = N::mad(omega, deq0 - d[0], d[0]);
     out[1] = N::mad(omega, deq1 - d[1], d[1]);
     out[2] = N::mad(omega, deq2 - d[2], d[2]);
-    return plain_status<T, 3>(out, W, rho0);
+    // per-population compares (measured faster than the sign-bit test in
+    // the bandwidth-bound D1Q3 kernel)
+    typename N::Pred all;
+    if constexpr (N::LANES == 1) all = true;
+    else all = {true, true};
+    return lane_status<T>(all, finite_nonneg<T, 3>(out, W, rho0));
 }
 
 // Dispatch by lattice and rule.

@@ -407,11 +407,7 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
         const int smask = (1 << sl2) - 1;  // last unit of a row
         const Rates<CT> rates{CT(p.omega), CT(p.omega2), CT(p.s_e), CT(p.s_eps)};
         uint32_t n_skip = 0, n_unst = 0;
-        float lid[Q];
-        if (bc == BC_CAVITY) {
-#pragma unroll
-            for (int a = 0; a < Q; ++a) lid[a] = p.lid[a];
-        }
+        const float* lid = p.lid;  // read where a lid node needs it
         const int inst = p.inst;
         // one unit at a time (unrolling raises register pressure and measured slower)
 #pragma unroll 1
