@@ -578,6 +578,10 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
         in.s_e = o.collision == COLL_MRT ? 1.64 : in.omega;
         in.s_eps = o.collision == COLL_MRT ? 1.54 : in.omega;
         in.u_lid = u_lid ? u_lid[i] : 0.0;
+        in.rates_f[0] = (float)in.omega;
+        in.rates_f[1] = (float)in.omega2;
+        in.rates_f[2] = (float)in.s_e;
+        in.rates_f[3] = (float)in.s_eps;
         if (bc == LBM_BC_CAVITY) {
             lid_deviation(o.rho0, in.u_lid, in.lid_dev);
             for (int a = 0; a < 9; ++a) in.lid_dev_f[a] = (float)in.lid_dev[a];

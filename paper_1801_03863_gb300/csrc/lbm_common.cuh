@@ -88,7 +88,9 @@ template <> struct Store<__nv_bfloat16> {
 // ---------------------------------------------------------------------------
 // Launch descriptors (plain data, copied to the device once at create).
 // ---------------------------------------------------------------------------
-struct InstDesc {
+// 16-byte aligned and sized: the TMA step kernel copies it into shared
+// memory with one bulk copy per tile.
+struct alignas(16) InstDesc {
     int64_t off;        // element offset of plane 0 of this instance
     int64_t plane;      // elements per population plane (pitch * ny)
     int64_t node0;      // index of this instance's first node in concatenated host arrays
@@ -99,8 +101,10 @@ struct InstDesc {
     double u_lid;       // lid speed (cavity only)
     double lid_dev[9];  // f^eq_a(rho0, (u_lid, 0)) - W_a rho0, FP64
     float lid_dev_f[9]; // the same rounded to FP32
+    float rates_f[4];   // omega, omega2, s_e, s_eps rounded to FP32
     int32_t tile0, ntiles;  // this instance's tiles in the tile table
 };
+static_assert(sizeof(InstDesc) % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 struct TileDesc {
     int32_t inst;  // instance index

@@ -41,6 +41,8 @@
 //    fill cannot express, read their neighbours from global memory with the
 //    boundary rule.
 #pragma once
+#include <cstddef>
+
 #include "lbm_aux.h"
 #include "lbm_collide.cuh"
 #include "lbm_step.cuh"
@@ -77,22 +79,24 @@ struct SmemTile {
     // + room to round the dynamic base up to 128 bytes, per-stage tile
     // parameters and two mbarriers per stage
     static constexpr size_t PARAMS_OFF = STAGES_BYTES;
-    static constexpr size_t BARS_OFF = PARAMS_OFF + 128 * STAGES;
+    static constexpr size_t PARAMS_BYTES = 256;  // per stage
+    static constexpr size_t BARS_OFF = PARAMS_OFF + PARAMS_BYTES * STAGES;
     static constexpr size_t SMEM_BYTES = 128 + BARS_OFF + 16 * STAGES;
     static_assert(UNITS >= 1 && UNITS <= 4, "a unit's halo chunk parks at most 3 values");
     static_assert(HALO_OFF % 128 == 0 && PLANE_BYTES % 128 == 0,
                   "tile blocks and halo columns must stay 128-byte aligned");
 };
 
-// Parameters of the tile held by one stage, written by the producing thread
-// before it arms the stage's barrier (consumers read them after the wait).
+// Parameters of the tile held by one stage: its instance's descriptor,
+// copied in by TMA on the stage's full barrier, and the tile's place,
+// written by the producing thread before it arms the barrier (consumers
+// read both after the wait; the tensor stores read the place).
 struct StageParams {
-    int64_t off, pitch, plane;
-    int32_t inst, X, x0, y0, nx, ny, bc, R, xl2;  // xl2 = log2(X)
-    float omega, omega2, s_e, s_eps;
-    float lid[9];
+    InstDesc in;
+    int32_t inst, X, x0, y0;
 };
-static_assert(sizeof(StageParams) <= 128, "stage parameters must fit 128 bytes");
+static_assert(sizeof(StageParams) <= 256, "stage parameters must fit 256 bytes");
+static_assert(offsetof(StageParams, in) == 0, "the descriptor copy starts the slot");
 
 // Bounded spin limit of one mbarrier wait (each try_wait may itself suspend
 // for a while); a copy that has not landed by then is treated as lost.
@@ -140,6 +144,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0,
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
         "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int c0, int c1,
@@ -318,12 +329,11 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     // Thread 0 writes local tile j out of its stage (every warp is done
     // with it): one tensor store per plane, then a commit.
     auto store_tile = [&](int j) {
-        const TileDesc tile = args.tiles[blockIdx.x + j * G];
+        const StageParams& p = params[j % NS];
         const S* sbase = stage_base + (size_t)(j % NS) * TS::STAGE_ELEMS;
-        const void* map = &omaps[tile.inst];
+        const void* map = &omaps[p.inst];
 #pragma unroll
-        for (int a = 0; a < Q; ++a)
-            tma_store_3d(map, sbase + a * TS::PLANE_ELEMS, tile.cx0, tile.y0, a);
+        for (int a = 0; a < Q; ++a) tma_store_3d(map, sbase + a * TS::PLANE_ELEMS, p.x0, p.y0, a);
         bulk_commit();
     };
 
@@ -331,11 +341,14 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     // (release) it waits until every warp is done with the stage's previous
     // tile j - NS and hands that tile to the tensor stores; returns false
     // if the stage was not released in time.  Later (fill) it waits until
-    // TMA has read the stores' sources, stores the tile parameters and
-    // issues the plane and halo copies on the stage's full barrier.  In
+    // TMA has read the stores' sources, stores the tile's place and issues
+    // the descriptor, plane and halo copies on the stage's full barrier.  In
     // between, thread 0 collides a unit of its own, so the stores are read
-    // out while it computes.
+    // out while it computes.  The tile descriptor is fetched one fill ahead,
+    // so no global load waits in thread 0's path.
     int nstored = 0;  // local tiles handed to TMA stores (thread 0's count)
+    TileDesc next{};  // descriptor of the next tile to fill (thread 0)
+    if (tid == 0 && ntl > 0) next = args.tiles[blockIdx.x];
     auto release = [&](int j) -> bool {
         const int st = j % NS, fill = j / NS;
         if (fill == 0) return true;
@@ -347,26 +360,19 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     auto fill = [&](int j) {
         const int st = j % NS;
         bulk_wait_read();
-        const TileDesc tile = args.tiles[blockIdx.x + j * G];
-        const InstDesc& in = args.inst[tile.inst];
+        const TileDesc tile = next;
+        if (j + 1 < ntl) next = args.tiles[blockIdx.x + (j + 1) * G];
         StageParams& p = params[st];
         const int X = tile.pad, R = TS::TILE_NODES / X;
-        p.off = in.off; p.pitch = in.pitch; p.plane = in.plane;
         p.inst = tile.inst; p.X = X; p.x0 = tile.cx0; p.y0 = tile.y0;
-        p.nx = in.nx; p.ny = in.ny; p.bc = in.bc; p.R = R;
-        p.xl2 = 31 - __clz(X);
-        p.omega = (float)in.omega;
-        p.omega2 = (float)in.omega2;
-        p.s_e = (float)in.s_e;
-        p.s_eps = (float)in.s_eps;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) p.lid[a] = in.lid_dev_f[a];
-        const uint32_t bytes = (uint32_t)((Q * R * X + 6 * R * E) * sizeof(S));
+        const uint32_t bytes =
+            (uint32_t)((Q * R * X + 6 * R * E) * sizeof(S) + sizeof(InstDesc));
         S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
         const void* map = &tmaps[tile.inst];
         const void* hmap = &hmaps[tile.inst];
         fence_proxy_async_smem();  // consumers' accesses to this stage come first
         mbar_arrive_expect_tx(&full[st], bytes);
+        bulk_load(&p.in, &args.inst[tile.inst], (uint32_t)sizeof(InstDesc), &full[st]);
 #pragma unroll
         for (int a = 0; a < Q; ++a)
             tma_load_3d(sbase + a * TS::PLANE_ELEMS, map, tile.cx0, tile.y0 - D2Q9::vy(a), a,
@@ -400,14 +406,15 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
 
         const StageParams& p = params[st];
         const int X = p.X;
-        const int x0 = p.x0, y0 = p.y0, nx = p.nx, ny = p.ny, bc = p.bc;
-        const int64_t pitch = p.pitch, plane = p.plane, off = p.off;
+        const int x0 = p.x0, y0 = p.y0, nx = p.in.nx, ny = p.in.ny, bc = p.in.bc;
+        const int64_t pitch = p.in.pitch, plane = p.in.plane, off = p.in.off;
         unsigned char* sb = reinterpret_cast<unsigned char*>(stage_base + (size_t)st * TS::STAGE_ELEMS);
-        const int sl2 = p.xl2 - 6;         // log2 of the units per tile row
+        const int sl2 = 25 - __clz(X);     // log2 of the units per tile row (X / 64)
         const int smask = (1 << sl2) - 1;  // last unit of a row
-        const Rates<CT> rates{CT(p.omega), CT(p.omega2), CT(p.s_e), CT(p.s_eps)};
+        const Rates<CT> rates{CT(p.in.rates_f[0]), CT(p.in.rates_f[1]), CT(p.in.rates_f[2]),
+                              CT(p.in.rates_f[3])};
         uint32_t n_skip = 0, n_unst = 0;
-        const float* lid = p.lid;  // read where a lid node needs it
+        const float* lid = p.in.lid_dev_f;  // read where a lid node needs it
         const int inst = p.inst;
         // one unit at a time (unrolling raises register pressure and measured slower)
 #pragma unroll 1
