@@ -131,8 +131,8 @@ Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t
 }
 
 struct Carve {
-    size_t buf_bytes, inst_off, tiles_off, status_off, partials_off, stage_off, tmap_off, err_off,
-        total;
+    size_t buf_bytes, inst_off, tiles_off, status_off, partials_off, cons_off, stage_off, tmap_off,
+        err_off, total;
 };
 
 Carve carve(const Layout& L, int lattice, int storage, int count) {
@@ -149,6 +149,8 @@ Carve carve(const Layout& L, int lattice, int storage, int count) {
     p += al(sizeof(unsigned long long) * 2 * count);
     c.partials_off = p;
     p += al(sizeof(double) * 3 * (size_t)CONS_PARTIALS * count);
+    c.cons_off = p;  // (instance, partial) work list of the conservation reduction
+    p += al(sizeof(int2) * (size_t)CONS_PARTIALS * count);
     c.stage_off = p;
     p += al(sizeof(double) * std::max<int64_t>(3 * L.total_nodes, Q * L.total_nodes));
     c.tmap_off = p;  // four TMA tensor maps per instance: [buffer][tile | halo]
@@ -178,6 +180,8 @@ struct lbm_ctx {
     TileDesc* d_tiles = nullptr;
     unsigned long long* d_status = nullptr;
     double* d_partials = nullptr;
+    int2* d_cons = nullptr;  // conservation work list
+    int n_cons = 0;
     double* d_stage = nullptr;
     CUtensorMapOpaque* d_tmaps = nullptr;  // [buffer][tile | halo][instance]
     unsigned int* d_error = nullptr;
@@ -231,6 +235,8 @@ AuxArgs aux_args(const lbm_ctx* ctx) {
     a.pulled = ctx->post;
     a.status = ctx->d_status;
     a.stream = ctx->stream;
+    a.cons_items = ctx->d_cons;
+    a.cons_nitems = ctx->n_cons;
     return a;
 }
 
@@ -610,6 +616,7 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
     ctx->d_tiles = reinterpret_cast<TileDesc*>(ctx->mem + ctx->cv.tiles_off);
     ctx->d_status = reinterpret_cast<unsigned long long*>(ctx->mem + ctx->cv.status_off);
     ctx->d_partials = reinterpret_cast<double*>(ctx->mem + ctx->cv.partials_off);
+    ctx->d_cons = reinterpret_cast<int2*>(ctx->mem + ctx->cv.cons_off);
     ctx->d_stage = reinterpret_cast<double*>(ctx->mem + ctx->cv.stage_off);
     ctx->d_tmaps = reinterpret_cast<CUtensorMapOpaque*>(ctx->mem + ctx->cv.tmap_off);
     ctx->d_error = reinterpret_cast<unsigned int*>(ctx->mem + ctx->cv.err_off);
@@ -621,6 +628,16 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
         return fail(LBM_ERR_CUDA);
     if (cudaMemsetAsync(ctx->mem, 0, ctx->cv.total, ctx->stream) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
+    {
+        std::vector<int2> items;
+        for (int i = 0; i < count; ++i)
+            for (int b = 0; b < cons_partials(ctx->layout.inst[i].ny); ++b) items.push_back({i, b});
+        ctx->n_cons = (int)items.size();
+        if (cudaMemcpyAsync(ctx->d_cons, items.data(), sizeof(int2) * items.size(),
+                            cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return fail(LBM_ERR_CUDA);
+    }
     Shape s;
     if (parse_shape_env(&s)) rc = apply_shape(ctx, s);
     else if (o.autotune && !getenv("LBM_NO_AUTOTUNE")) rc = autotune(ctx);

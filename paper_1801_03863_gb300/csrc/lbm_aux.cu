@@ -204,52 +204,71 @@ __device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, 
     }
 }
 
-// Conservation, pass 1: block b of instance i sums (sum d, sum d v_x,
-// sum d v_y) over nodes k = b*256 + t + j*P*256 and reduces the block in a
-// fixed tree; partials[(i*P + b)*3 + c].  The grid (P blocks per instance)
-// is a constant, so the summation order is fixed.  Every sum runs in FP64,
-// except the node-level sums of 2-byte storage, which add the nine 11- or
-// 8-bit-significand deviations in FP32 (error below 9 * 2^-24 * sum |d|, far
-// under the storage rounding itself) before the FP64 sums across nodes.
+// Conservation, pass 1: the block of work item (i, b) sums (sum d,
+// sum d v_x, sum d v_y) of f(t_n) over the rows y = b mod P_i of instance i
+// (P_i = cons_partials(ny_i)); thread t takes x = t, t + CONS_THREADS, ...
+// of each of those rows, rows in increasing order, and the block reduces
+// its threads in a fixed tree into partials[(i*CONS_PARTIALS + b)*3 + c].
+// The order is fixed by the instance alone.  Every sum runs in FP64, except
+// the node-level sums of 2-byte storage, which add the nine 11- or
+// 8-bit-significand deviations in FP32 (error below 9 * 2^-24 * sum |d|,
+// far under the storage rounding itself) before the FP64 sums across
+// nodes.  Interior nodes pull with plain shifted loads; the outer ring
+// applies the boundary rules.
 template <class Lat, typename S>
-__global__ void __launch_bounds__(AUX_THREADS)
-cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* partials) {
-    __shared__ double sh[3][AUX_THREADS];
-    const InstDesc in = insts[blockIdx.y];
-    const int64_t n = (int64_t)in.nx * in.ny;
+__global__ void __launch_bounds__(CONS_THREADS)
+cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool pulled,
+                    double* partials) {
+    using V = typename std::conditional<sizeof(S) == 2, float, double>::type;
+    __shared__ double sh[3][CONS_THREADS];
+    const int2 it = items[blockIdx.x];
+    const InstDesc in = insts[it.x];
+    const int nx = in.nx, ny = in.ny, P = cons_partials(ny);
+    const S* base = src + in.off;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * AUX_THREADS + threadIdx.x; k < n;
-         k += (int64_t)CONS_PARTIALS * AUX_THREADS) {
-        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
-        if constexpr (sizeof(S) >= 4) {
-            double d[Lat::Q];
-            node_state<Lat, S>(src, in, x, y, pulled, d);
+    for (int y = it.y; y < ny; y += P) {
+        const bool yint = Lat::Q == 3 || (y >= 1 && y <= ny - 2);
+        for (int x = threadIdx.x; x < nx; x += CONS_THREADS) {
+            V d[Lat::Q];
+            if (!pulled || (yint && x >= 1 && x <= nx - 2)) {
 #pragma unroll
-            for (int a = 0; a < Lat::Q; ++a) {
-                s0 += d[a];
-                if (Lat::vx(a) != 0) s1 += Lat::vx(a) * d[a];
-                if (Lat::vy(a) != 0) s2 += Lat::vy(a) * d[a];
+                for (int a = 0; a < Lat::Q; ++a) {
+                    const int sx = pulled ? x - Lat::vx(a) : x, sy = pulled ? y - Lat::vy(a) : y;
+                    const S v = base[(int64_t)a * in.plane + (int64_t)sy * in.pitch + sx];
+                    if constexpr (sizeof(S) == 2) d[a] = Store<S>::to_f32(v);
+                    else d[a] = Store<S>::to_f64(v);
+                }
+            } else if constexpr (sizeof(S) == 2) {
+                node_state_f32<Lat, S>(src, in, x, y, pulled, d);
+            } else {
+                node_state<Lat, S>(src, in, x, y, pulled, d);
             }
-        } else {
-            float d[Lat::Q];
-            node_state_f32<Lat, S>(src, in, x, y, pulled, d);
-            float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+            if constexpr (sizeof(S) >= 4) {
 #pragma unroll
-            for (int a = 0; a < Lat::Q; ++a) {
-                r0 += d[a];
-                if (Lat::vx(a) != 0) r1 += (float)Lat::vx(a) * d[a];
-                if (Lat::vy(a) != 0) r2 += (float)Lat::vy(a) * d[a];
+                for (int a = 0; a < Lat::Q; ++a) {
+                    s0 += d[a];
+                    if (Lat::vx(a) != 0) s1 += Lat::vx(a) * d[a];
+                    if (Lat::vy(a) != 0) s2 += Lat::vy(a) * d[a];
+                }
+            } else {
+                float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < Lat::Q; ++a) {
+                    r0 += d[a];
+                    if (Lat::vx(a) != 0) r1 += (float)Lat::vx(a) * d[a];
+                    if (Lat::vy(a) != 0) r2 += (float)Lat::vy(a) * d[a];
+                }
+                s0 += (double)r0;
+                s1 += (double)r1;
+                s2 += (double)r2;
             }
-            s0 += (double)r0;
-            s1 += (double)r1;
-            s2 += (double)r2;
         }
     }
     sh[0][threadIdx.x] = s0;
     sh[1][threadIdx.x] = s1;
     sh[2][threadIdx.x] = s2;
     __syncthreads();
-    for (int h = AUX_THREADS / 2; h > 0; h >>= 1) {
+    for (int h = CONS_THREADS / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + h];
@@ -257,8 +276,7 @@ cons_partial_kernel(const S* src, const InstDesc* insts, bool pulled, double* pa
         __syncthreads();
     }
     if (threadIdx.x < 3)
-        partials[((int64_t)blockIdx.y * CONS_PARTIALS + blockIdx.x) * 3 + threadIdx.x] =
-            sh[threadIdx.x][0];
+        partials[((int64_t)it.x * CONS_PARTIALS + it.y) * 3 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // Conservation, pass 2: one thread per instance adds its partials in order;
@@ -268,7 +286,8 @@ __global__ void cons_final_kernel(const double* partials, const InstDesc* insts,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     double s[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < CONS_PARTIALS; ++b)
+    const int P = cons_partials(insts[i].ny);
+    for (int b = 0; b < P; ++b)
         for (int c = 0; c < 3; ++c) s[c] += partials[((int64_t)i * CONS_PARTIALS + b) * 3 + c];
     const double nodes = (double)insts[i].nx * (double)insts[i].ny;
     out[3 * i + 0] = nodes * rho0 + s[0];
@@ -329,8 +348,9 @@ cudaError_t aux_dispatch(AuxOp op, const AuxArgs& a, const void* src, void* dst,
                                                                      a.inst, a.pulled, a.rho0, o0);
             break;
         case AuxOp::Conservation: {
-            cons_partial_kernel<Lat, S><<<dim3(CONS_PARTIALS, a.count), AUX_THREADS, 0, a.stream>>>(
-                static_cast<const S*>(src), a.inst, a.pulled, o1);
+            if (a.cons_nitems < 1 || !a.cons_items) return cudaErrorInvalidValue;
+            cons_partial_kernel<Lat, S><<<a.cons_nitems, CONS_THREADS, 0, a.stream>>>(
+                static_cast<const S*>(src), a.inst, a.cons_items, a.pulled, o1);
             cons_final_kernel<<<(a.count + 127) / 128, 128, 0, a.stream>>>(o1, a.inst, a.count,
                                                                            a.rho0, o0);
             break;

@@ -7,9 +7,13 @@
 
 namespace lbm {
 
-// Blocks per instance of the first conservation pass (fixed, so the FP64
-// summation order never depends on the device).
+// Conservation reduction: instance i is split into P_i = min(CONS_PARTIALS,
+// ny_i) partial sums, partial b over the rows y = b mod P_i, each summed by
+// one block of CONS_THREADS threads; the split is a function of the instance
+// alone, so the FP64 summation order never depends on the device.
 constexpr int CONS_PARTIALS = 64;
+constexpr int CONS_THREADS = 1024;
+__host__ __device__ inline int cons_partials(int ny) { return ny < CONS_PARTIALS ? ny : CONS_PARTIALS; }
 
 enum class AuxOp { Init, SetF, CollideInPlace, Moments, GatherF, Conservation };
 
@@ -25,6 +29,8 @@ struct AuxArgs {
     bool pulled;           // stored field is post-collision (pull to read f(t_n))
     unsigned long long* status;
     cudaStream_t stream;
+    const int2* cons_items;  // device: (instance, partial) of each conservation block
+    int32_t cons_nitems;
 };
 
 // Init:           dst <- f^eq(rho=p0, ux=p1, uy=p2) deviations
@@ -33,7 +39,8 @@ struct AuxArgs {
 // Moments:        o0, o1, o2 <- rho, ux, uy of f(t_n) read from src
 // GatherF:        o0 <- FP64 populations of f(t_n)
 // Conservation:   o0 <- per-instance totals (3 doubles each), o1 = partials scratch
-//                 (count * CONS_PARTIALS * 3 doubles)
+//                 (count * CONS_PARTIALS * 3 doubles; partial b of instance i at
+//                 (i * CONS_PARTIALS + b) * 3)
 cudaError_t run_aux(AuxOp op, const AuxArgs& a, const void* src, void* dst, const double* p0,
                     const double* p1, const double* p2, double* o0, double* o1, double* o2);
 
