@@ -393,11 +393,24 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
     return a;
 }
 
+// One step launch.  It is a programmatic dependent launch: the kernel may be
+// scheduled while the previous kernel in the stream drains, and waits for its
+// completion (griddepcontrol.wait) before touching device state.
 cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
     StepArgs a = step_args(ctx, src);
     void* params[] = {&a};
     const int block = ctx->shape.kind >= 1 ? 256 : ctx->shape.tw * ctx->shape.th;
-    return cudaLaunchKernel(ctx->kern, dim3(ctx->grid), dim3(block), params, ctx->smem, s);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctx->grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = ctx->smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, ctx->kern, params);
 }
 
 // Time candidate shapes on the zeroed (rest-state) buffers and keep the fastest.

@@ -138,4 +138,17 @@ struct StepArgs {
 
 __host__ __device__ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Programmatic dependent launch between consecutive step kernels: a step
+// kernel may be scheduled while the previous one drains; it runs its
+// prologue, then waits here until the previous kernel in the stream has
+// completed and its writes are visible, before it touches the population
+// buffers, counters or error word.  Without a programmatic launch both are
+// no-ops.
+__device__ __forceinline__ void wait_previous_grid() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_next_grid() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace lbm

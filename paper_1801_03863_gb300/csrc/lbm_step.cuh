@@ -159,6 +159,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
     const int cy = tid >> args.tw_log2;
     const int lane = tid & 31;
     const T rho0 = (T)args.rho0;
+    wait_previous_grid();
+    allow_next_grid();
 
     for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x) {
         const TileDesc tile = args.tiles[t];

@@ -349,6 +349,10 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     int nstored = 0;  // local tiles handed to TMA stores (thread 0's count)
     TileDesc next{};  // descriptor of the next tile to fill (thread 0)
     if (tid == 0 && ntl > 0) next = args.tiles[blockIdx.x];
+    // the tile table and tensor maps are constant; the populations, counters
+    // and error word are read and written only after this
+    wait_previous_grid();
+    allow_next_grid();
     auto release = [&](int j) -> bool {
         const int st = j % NS, fill = j / NS;
         if (fill == 0) return true;
