@@ -222,7 +222,8 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * with large tiles, 2048 nodes for 2-byte storage or 1024 for FP32, on a
  * two-stage ring; 2: the same kernel with small tiles, 1024 / 512 nodes, on
  * a three-stage ring.  For kinds 1 and 2 the tile width is 64/128/256 nodes
- * chosen per instance and out[1], out[2] are 0).  Selection: the create-time
+ * chosen per instance, at most an eighth of the tile, and out[1], out[2] are
+ * 0; tiles go in and out of shared memory by TMA).  Selection: the create-time
  * autotuner, or the environment variable LBM_SHAPE = "V,tw,th" (register
  * chunks), "smem" (kind 1) or "smems" (kind 2). */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* out);
