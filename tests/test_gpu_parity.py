@@ -147,6 +147,61 @@ def test_one_step_random_states_fp64(bc):
             assert linf <= TOL64, (k, linf)
 
 
+# Lattices of one to a few nodes per side, as one uneven ensemble: every node
+# is an edge node, tile rows are mostly padding, and x shifts wrap or clamp
+# onto the node itself.  Cavities need an interior node (3 x 3 at least).
+_TINY = {"periodic": [(1, 1), (2, 3), (5, 2), (1, 9), (9, 1), (3, 3)],
+         "zero_gradient": [(1, 1), (2, 3), (5, 2), (1, 9), (9, 1), (3, 3)],
+         "cavity": [(3, 3), (4, 3), (3, 5), (17, 4)]}
+
+
+def _tiny_state(dims):
+    parts = [wl.random_populations(9, ny, nx, eps=0.2, seed=5 + i)
+             for i, (nx, ny) in enumerate(dims)]
+    return parts, np.concatenate([p.ravel() for p in parts])
+
+
+@pytest.mark.parametrize("bc", ["periodic", "zero_gradient", "cavity"])
+def test_tiny_lattices_fp64_match_oracle(bc):
+    dims = _TINY[bc]
+    parts, f0 = _tiny_state(dims)
+    steps = 9
+    with lbm.Lattice("d2q9", dims, 0.02, bc, u_lid=0.08) as lat:
+        lat.set_populations(f0)
+        lat.step(steps)
+        f = lat.populations()
+    k = 0
+    for i, (nx, ny) in enumerate(dims):
+        n = 9 * nx * ny
+        sim = oracle.Sim(oracle.D2Q9, nx, ny, oracle.tau_from_nu(0.02), _orc_bc(bc), u_lid=0.08)
+        sim.set_f(parts[i])
+        sim.step(steps)
+        linf, _ = _rel(f[k:k + n], sim.get_f())
+        assert linf <= TOL64, (bc, nx, ny, linf)
+        k += n
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("bc", ["periodic", "zero_gradient", "cavity"])
+def test_tiny_lattices_kernels_agree_bitwise(storage, bc, monkeypatch):
+    """The TMA kernel (both tile geometries) and the register-chunk kernel
+    agree bit for bit on the tiny ensemble."""
+    dims = _TINY[bc]
+    _, f0 = _tiny_state(dims)
+    chunk = "2,16,8" if storage == "f32" else "4,8,16"
+    out = {}
+    for s in (chunk, "smem", "smems"):
+        monkeypatch.setenv("LBM_SHAPE", s)
+        with lbm.Lattice("d2q9", dims, 0.02, bc, u_lid=0.08, compute="f32",
+                         storage=storage) as lat:
+            lat.set_populations(f0)
+            lat.step(9)
+            out[s] = (lat.populations(), lat.status())
+    for s in ("smem", "smems"):
+        assert out[s][1] == out[chunk][1], s
+        assert np.array_equal(out[s][0], out[chunk][0]), s
+
+
 # ----------------------------------------------------------------------------
 # Ensembles: one persistent launch over uneven instances.
 # ----------------------------------------------------------------------------
