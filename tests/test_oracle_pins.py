@@ -473,3 +473,46 @@ def test_stream_function_matches_library_simpson_and_converges(orc):
         # error relative to the integral's scale L (spacing h = 1/L)
         errs.append(np.abs(orc.stream_function(u)[0, 0::2] - exact[0::2]).max() / L)
     assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14, errs
+
+
+def _table3(golden_dir):
+    rows = {}
+    for line in open(os.path.join(golden_dir, "table3_rates.txt")):
+        line = line.split("#")[0].split()
+        if line:
+            rows[line[0]] = line[1:]
+    return rows
+
+
+def _rate(token: str, tau: float, tau2: float) -> float:
+    return {"1/tau": 1.0 / tau, "1/tau2": 1.0 / tau2}.get(token) or float(token)
+
+
+@pytest.mark.parametrize("rule", ["MRT", "TRT"])
+@pytest.mark.parametrize("tau", [0.6, 0.7])
+@pytest.mark.parametrize("reading", ["printed", "magic"])
+def test_mrt_trt_rates_match_table3(orc, golden_dir, rule, tau, reading):
+    """Table III, one moment at a time.  Start from f^eq(rho, u) and add
+    eps rho (T^-1)_{:,k} for one non-conserved moment k (this leaves rho and u,
+    hence f^eq, unchanged).  Eq. (mrtcollision) then moves only moment k,
+    T (f^post - f^eq) = eps rho (1 - B_k) e_k, so B_k is read off and compared
+    with the printed table; T^-1 here is numpy's inverse of the printed T.
+    tau2 differs from tau under both readings of Eq. (tau2)."""
+    T = np.loadtxt(os.path.join(golden_dir, "tmatrix.txt"))
+    Tinv = np.linalg.inv(T)
+    tau2 = (8 * tau - 1) / ((8.0 if reading == "magic" else 1.0) * (2 * tau - 1))
+    assert abs(tau2 - tau) > 0.05
+    table = _table3(golden_dir)[rule]
+    rho, ux, uy, eps = 1.3, 0.04, -0.03, 1e-3
+    feq = orc.d2q9_feq(rho, ux, uy)
+    for k in range(9):
+        if k in (0, 3, 5):  # mass and momentum: fixed by the conservation pins
+            assert table[k] == "0"
+            continue
+        f = feq + eps * rho * Tinv[:, k]
+        post, st = orc.d2q9_mrt(f, tau, trt=(rule == "TRT"), tau2_=tau2)
+        assert st == 0
+        m = T @ (post - feq) / (eps * rho)
+        want = np.zeros(9)
+        want[k] = 1.0 - _rate(table[k], tau, tau2)
+        assert np.max(np.abs(m - want)) < 1e-10, (k, m, want)
