@@ -86,6 +86,10 @@ def _load():
             "orc_counters": (None, [P, P]),
             "orc_num_threads": (I, []),
             "orc_stream_function": (None, [I, I, P, P]),
+            "orc_set_slab": (I, [P, I, I]),
+            "orc_collide": (None, [P]),
+            "orc_stream": (None, [P, P, P]),
+            "orc_post_row": (None, [P, I, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -277,6 +281,29 @@ class Sim:
 
     def step(self, n: int = 1):
         self._lib.orc_step(self._h, int(n))
+
+    # -- slab form: rows [y_off, y_off + ny) of a lattice of ny_global rows
+    def set_slab(self, y_off: int, ny_global: int):
+        if self._lib.orc_set_slab(self._h, int(y_off), int(ny_global)) != 0:
+            raise ValueError("slab rows outside the lattice")
+
+    def collide(self):
+        """First half of Eq. (2): collide every node of this lattice."""
+        self._lib.orc_collide(self._h)
+
+    def post_row(self, y: int) -> np.ndarray:
+        """Post-collision populations of local row y after collide(), [a][x]."""
+        out = np.zeros((self.q, self.nx))
+        self._lib.orc_post_row(self._h, int(y), _ptr(out))
+        return out
+
+    def stream(self, lo=None, hi=None):
+        """Second half of Eq. (2); lo / hi: post-collision rows below the first
+        and above the last row ([a][x]), or None for the lattice's own rule."""
+        lo = None if lo is None else _f64(lo).reshape(self.q, self.nx)
+        hi = None if hi is None else _f64(hi).reshape(self.q, self.nx)
+        self._lib.orc_stream(self._h, None if lo is None else _ptr(lo),
+                             None if hi is None else _ptr(hi))
 
     def moments(self):
         rho = np.zeros((self.ny, self.nx))

@@ -538,6 +538,9 @@ typedef struct {
     double* f; /* pre-collision populations f(x, t_n), [node][q] */
     double* g; /* post-collision scratch */
     long long n_skipped, n_unstable, steps;
+    /* Slab of a taller lattice (orc_set_slab): local row y is global row
+     * y + y_off of ny_global rows. */
+    int y_off, ny_global;
 } orc_sim;
 
 ORC_EXPORT double orc_tau_from_nu(double nu) {
@@ -563,6 +566,8 @@ ORC_EXPORT orc_sim* orc_create(int lattice, int nx, int ny, double tau, int bc, 
     s->tau2 = orc_tau2(tau);
     s->rho0 = rho0;
     s->u_lid = u_lid;
+    s->y_off = 0;
+    s->ny_global = ny;
     size_t n = (size_t)nx * ny * s->q;
     s->f = (double*)calloc(n, sizeof(double));
     s->g = (double*)calloc(n, sizeof(double));
@@ -611,8 +616,9 @@ ORC_EXPORT void orc_get_f(const orc_sim* s, double* f) {
 enum { NODE_FLUID = 0, NODE_WALL = 1, NODE_LID = 2 };
 static int node_class(const orc_sim* s, int x, int y) {
     if (s->bc != ORC_BC_CAVITY) return NODE_FLUID;
-    if (x == 0 || x == s->nx - 1 || y == 0) return NODE_WALL;
-    if (y == s->ny - 1) return NODE_LID;
+    const int yg = y + s->y_off; /* row in the whole lattice */
+    if (x == 0 || x == s->nx - 1 || yg == 0) return NODE_WALL;
+    if (yg == s->ny_global - 1) return NODE_LID;
     return NODE_FLUID;
 }
 
@@ -635,7 +641,8 @@ static int collide_node(const orc_sim* s, const double* f, double* g) {
 }
 
 /*
- * n time steps of Eq. (2): collide every node, then stream.
+ * One time step of Eq. (2), in its two halves: collide every node, then
+ * stream.
  *
  * Collision (per node class, Sec. IV.F):
  *   fluid: the configured collision rule;
@@ -648,64 +655,104 @@ static int collide_node(const orc_sim* s, const double* f, double* g) {
  *     copy of the end node's post-collision populations;
  *   cavity: a source outside the lattice (only ring nodes have one) gives
  *     W_a rho0 (reading; such values never reach a fluid node).
+ * A slab (orc_set_slab) streams across its lower / upper edge from the halo
+ * rows lo / hi: the post-collision row below its first row and above its
+ * last one, as the neighbouring slabs computed them ([a][x], q * nx values;
+ * NULL = the boundary rule of the lattice applies at that edge).
  */
-ORC_EXPORT void orc_step(orc_sim* s, int nsteps) {
+static void collide_pass(orc_sim* s) {
     const int q = s->q, nx = s->nx, ny = s->ny;
-    for (int it = 0; it < nsteps; ++it) {
-        long long skipped = 0, unstable = 0;
-        /* collide */
+    long long skipped = 0, unstable = 0;
 #pragma omp parallel for reduction(+ : skipped, unstable) schedule(static)
-        for (int y = 0; y < ny; ++y) {
-            for (int x = 0; x < nx; ++x) {
-                size_t i = (size_t)y * nx + x;
-                const double* f = s->f + i * q;
-                double* g = s->g + i * q;
-                int cls = node_class(s, x, y);
-                if (cls == NODE_WALL) {
-                    for (int a = 0; a < 9; ++a) g[a] = f[opp9(a)];
-                } else if (cls == NODE_LID) {
-                    orc_d2q9_feq(s->rho0, s->u_lid, 0.0, g);
-                } else {
-                    int st = collide_node(s, f, g);
-                    if (st & ORC_NEWTON_SKIPPED) ++skipped;
-                    if (st & ORC_UNSTABLE) ++unstable;
-                }
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            size_t i = (size_t)y * nx + x;
+            const double* f = s->f + i * q;
+            double* g = s->g + i * q;
+            int cls = node_class(s, x, y);
+            if (cls == NODE_WALL) {
+                for (int a = 0; a < 9; ++a) g[a] = f[opp9(a)];
+            } else if (cls == NODE_LID) {
+                orc_d2q9_feq(s->rho0, s->u_lid, 0.0, g);
+            } else {
+                int st = collide_node(s, f, g);
+                if (st & ORC_NEWTON_SKIPPED) ++skipped;
+                if (st & ORC_UNSTABLE) ++unstable;
             }
         }
-        s->n_skipped += skipped;
-        s->n_unstable += unstable;
-        /* stream */
-#pragma omp parallel for schedule(static)
-        for (int y = 0; y < ny; ++y) {
-            for (int x = 0; x < nx; ++x) {
-                size_t i = (size_t)y * nx + x;
-                for (int a = 0; a < q; ++a) {
-                    int vx = (q == 9) ? V9[a][0] : V3[a];
-                    int vy = (q == 9) ? V9[a][1] : 0;
-                    int sx = x - vx, sy = y - vy;
-                    double val;
-                    if (s->bc == ORC_BC_PERIODIC) {
-                        sx = (sx % nx + nx) % nx;
-                        sy = (sy % ny + ny) % ny;
-                        val = s->g[((size_t)sy * nx + sx) * q + a];
-                    } else if (s->bc == ORC_BC_ZERO_GRADIENT) {
-                        /* ghost -1 copies node 0, ghost nx copies node nx-1 */
-                        if (sx < 0) sx = 0;
-                        if (sx > nx - 1) sx = nx - 1;
-                        sy = (sy % ny + ny) % ny;
-                        val = s->g[((size_t)sy * nx + sx) * q + a];
-                    } else {
-                        if (sx < 0 || sx >= nx || sy < 0 || sy >= ny)
-                            val = W9[a] * s->rho0;
-                        else
-                            val = s->g[((size_t)sy * nx + sx) * q + a];
-                    }
-                    s->f[i * q + a] = val;
-                }
-            }
-        }
-        s->steps += 1;
     }
+    s->n_skipped += skipped;
+    s->n_unstable += unstable;
+}
+
+static void stream_pass(orc_sim* s, const double* lo, const double* hi) {
+    const int q = s->q, nx = s->nx, ny = s->ny;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            size_t i = (size_t)y * nx + x;
+            for (int a = 0; a < q; ++a) {
+                int vx = (q == 9) ? V9[a][0] : V3[a];
+                int vy = (q == 9) ? V9[a][1] : 0;
+                int sx = x - vx, sy = y - vy;
+                const double* halo = (sy < 0) ? lo : ((sy >= ny) ? hi : NULL);
+                double val;
+                if (s->bc == ORC_BC_PERIODIC) {
+                    sx = (sx % nx + nx) % nx;
+                    sy = (sy % ny + ny) % ny;
+                    val = halo ? halo[(size_t)a * nx + sx] : s->g[((size_t)sy * nx + sx) * q + a];
+                } else if (s->bc == ORC_BC_ZERO_GRADIENT) {
+                    /* ghost -1 copies node 0, ghost nx copies node nx-1 */
+                    if (sx < 0) sx = 0;
+                    if (sx > nx - 1) sx = nx - 1;
+                    sy = (sy % ny + ny) % ny;
+                    val = halo ? halo[(size_t)a * nx + sx] : s->g[((size_t)sy * nx + sx) * q + a];
+                } else {
+                    if (sx < 0 || sx >= nx)
+                        val = W9[a] * s->rho0;
+                    else if (halo)
+                        val = halo[(size_t)a * nx + sx];
+                    else if (sy < 0 || sy >= ny)
+                        val = W9[a] * s->rho0;
+                    else
+                        val = s->g[((size_t)sy * nx + sx) * q + a];
+                }
+                s->f[i * q + a] = val;
+            }
+        }
+    }
+    s->steps += 1;
+}
+
+/* n time steps of Eq. (2) on the whole lattice. */
+ORC_EXPORT void orc_step(orc_sim* s, int nsteps) {
+    for (int it = 0; it < nsteps; ++it) {
+        collide_pass(s);
+        stream_pass(s, NULL, NULL);
+    }
+}
+
+/* The slab form: this lattice is rows [y_off, y_off + ny) of one of
+ * ny_global rows, for the node classes of the cavity (bottom wall at global
+ * row 0, lid at global row ny_global - 1). */
+ORC_EXPORT int orc_set_slab(orc_sim* s, int y_off, int ny_global) {
+    if (y_off < 0 || ny_global < y_off + s->ny) return -1;
+    s->y_off = y_off;
+    s->ny_global = ny_global;
+    return 0;
+}
+
+/* The two halves of one step, for a slab that exchanges its edge rows in
+ * between: orc_collide, then orc_post_row of its first and last rows to the
+ * neighbours, then orc_stream with the rows received from them. */
+ORC_EXPORT void orc_collide(orc_sim* s) { collide_pass(s); }
+ORC_EXPORT void orc_stream(orc_sim* s, const double* lo, const double* hi) {
+    stream_pass(s, lo, hi);
+}
+/* Post-collision populations of local row y, [a][x]. */
+ORC_EXPORT void orc_post_row(const orc_sim* s, int y, double* out) {
+    for (int a = 0; a < s->q; ++a)
+        for (int x = 0; x < s->nx; ++x) out[(size_t)a * s->nx + x] = s->g[((size_t)y * s->nx + x) * s->q + a];
 }
 
 /* Macroscopic fields of f(x, t_n) (Sec. II.A): rho = sum f, rho u = sum f v. */
