@@ -119,15 +119,18 @@ DEFAULT_STORAGE = {"ensemble64": "f16", "cavity2048": "f16", "tg512": "f32", "tu
 class Workload:
     """Lattice parameters and initial fields of this rank's share."""
 
-    def __init__(self, name: str, rank: int, world: int):
+    def __init__(self, name: str, rank: int, world: int, members_per_gpu: int | None = None):
         from paper_1801_03863_gb300 import workloads as wl
         from paper_1801_03863_gb300.partition import partition
         self.name = name
         self.lattice, self.bc = "d2q9", "cavity"
         self.u_lid = None
+        self.member_ids = [0]
         if name == "ensemble64":
-            members = wl.cavity_ensemble(count=MEMBERS_PER_GPU * world, seed=0)
+            per = members_per_gpu or MEMBERS_PER_GPU
+            members = wl.cavity_ensemble(count=per * world, seed=0)
             mine = partition([m.side * m.side for m in members], world)[rank]
+            self.member_ids = list(mine)
             self.members = [members[i] for i in mine]
             self.dims = [(m.side, m.side) for m in self.members]
             self.nu = [m.nu for m in self.members]
@@ -148,8 +151,9 @@ class Workload:
             self.rho, self.ux, self.uy = r.ravel(), x.ravel(), y.ravel()
         elif name == "tubes4096":
             self.lattice, self.bc = "d1q3", "zero_gradient"
-            members = wl.tube_ensemble(count=4096 * world, seed=1)
+            members = wl.tube_ensemble(count=(members_per_gpu or 4096) * world, seed=1)
             mine = partition([m.n for m in members], world)[rank]
+            self.member_ids = list(mine)
             self.dims = [(members[i].n, 1) for i in mine]
             self.nu = [members[i].nu for i in mine]
             self.rho = np.concatenate([wl.tube_fields(members[i])[0].ravel() for i in mine])
