@@ -47,7 +47,12 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_ERR_NODEV (-6)    /* no CUDA device, or not an sm_103 device       */
 #define LBM_ERR_TIMEOUT (-7)  /* a bounded device-side wait on an asynchronous
                                  copy ran out; the step's outputs are invalid
-                                 (sticky, reported by lbm_status / lbm_moments) */
+                                 (sticky, reported by lbm_status / lbm_moments).
+                                 Test hooks, read at context creation: the
+                                 environment variable LBM_SPIN_LIMIT (1 .. 2^20)
+                                 shortens the waits, LBM_TEST_LOST_TILE = t makes
+                                 the TMA-staged kernel skip the copies of tile t,
+                                 so that its waits run out without any fault */
 
 /* Lattices: D2Q9 of Table I; D1Q3, its one-dimensional restriction
  * (velocities 0, +1, -1; weights 2/3, 1/6, 1/6). */
@@ -140,26 +145,55 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
 
 /* Initial populations at equilibrium (Sec. IV.F) from host FP64 fields
  * rho, ux, uy (each sum(nx*ny) long, instances concatenated); ux/uy may be
- * NULL for zero; uy is ignored on D1Q3.  Resets the status counters. */
+ * NULL for zero; uy is ignored on D1Q3.  Resets the status counters.
+ * Page-locked host arrays (cudaHostAlloc, cudaHostRegister) are read in
+ * place by the initialising kernel; other host memory is first copied to a
+ * device staging area.  Synchronises. */
 int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 
 /* Same as lbm_init with DEVICE pointers, ordered on the context's stream;
  * does not synchronise. */
 int lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 
+/* Initial populations of ONE instance of an ensemble at equilibrium
+ * (Sec. IV.F: f = f^eq(rho, u), Eq. numerical-plyeqm) from host FP64 fields
+ * of that instance alone (nx*ny values each, [y][x]; ux/uy may be NULL for
+ * zero; uy is ignored on D1Q3).  The other instances are left untouched and
+ * the instance's status counters are reset.  Allowed before the first step
+ * after context creation, lbm_init or lbm_set_populations (LBM_ERR_STATE
+ * once the context has stepped: the stored field is then post-collision).
+ * The context counts as initialised once every instance has been set, by
+ * this call or by lbm_init.  Synchronises. */
+int lbm_init_batch(lbm_ctx* ctx, int32_t instance, const double* rho, const double* ux,
+                   const double* uy);
+
 /* Advance every instance by n >= 0 time steps (Eq. 2).  Asynchronous on the
- * context's stream; long runs replay a captured CUDA graph. */
+ * context's stream; runs of 16 or more steps replay CUDA graphs of 16
+ * launches, captured and uploaded when the context is created. */
 int lbm_step(lbm_ctx* ctx, int64_t n);
 
 /* Density and velocity of f(x, t_n) (Sec. II.A: rho = sum f, rho u = sum f v)
  * into host FP64 arrays (sum(nx*ny) each; ux/uy may be NULL).  Synchronises
  * the stream; returns LBM_ERR_UNSTABLE if any instance has flagged an
- * unstable node since lbm_init (the fields are written all the same). */
+ * unstable node since lbm_init (the fields are written all the same).
+ * Page-locked host arrays are written in place by the moments kernel. */
 int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy);
 
 /* lbm_moments into DEVICE FP64 arrays, ordered on the stream, no sync and
  * no status check. */
 int lbm_moments_device(lbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Density and velocity of f(x, t_n) (Sec. II.A) of ONE instance into host
+ * FP64 arrays of nx*ny values ([y][x]; ux/uy may be NULL): the same values
+ * lbm_moments writes for that instance, without reading back the others.
+ * Synchronises; returns LBM_ERR_UNSTABLE if this instance has flagged an
+ * unstable node since it was initialised (fields written all the same). */
+int lbm_moments_batch(lbm_ctx* ctx, int32_t instance, double* rho, double* ux, double* uy);
+
+/* lbm_moments_batch into DEVICE FP64 arrays of nx*ny values, ordered on the
+ * stream, no sync and no status check. */
+int lbm_moments_batch_device(lbm_ctx* ctx, int32_t instance, double* rho, double* ux,
+                             double* uy);
 
 /* Stream function of f(x, t_n) for the lid-driven cavity analysis of
  * Sec. IV.I: per row of every instance, psi(x, y) = - integral from x = 0 to
@@ -175,12 +209,37 @@ int lbm_stream_function(lbm_ctx* ctx, double* psi);
  * sync and no status check (uses the context's staging area for u). */
 int lbm_stream_function_device(lbm_ctx* ctx, double* psi);
 
+/* lbm_stream_function of ONE instance (Sec. IV.I) into a host FP64 array
+ * of nx*ny values; the same values lbm_stream_function writes for that
+ * instance.  Synchronises; status as lbm_moments_batch. */
+int lbm_stream_function_batch(lbm_ctx* ctx, int32_t instance, double* psi);
+
 /* Populations f(x, t_n) to / from host FP64, layout per instance
  * [a][y][x] (a in the order rest, +x, +y, -x, -y, (+x,+y), (-x,+y),
  * (-x,-y), (+x,-y) for D2Q9; rest, +x, -x for D1Q3), instances
- * concatenated.  set_populations replaces the state (checkpoint / resume). */
+ * concatenated.  set_populations replaces the state; the next step collides
+ * the loaded f(x, t_n) in place with the step kernels' arithmetic, so a
+ * state read with get_populations and set into another context continues
+ * bit for bit when its FP64 values round-trip exactly (always for FP16 and
+ * BF16 storage; FP32 and FP64 deviations far below W_a rho0 lose bits in
+ * f = W_a rho0 + d -- lbm_save_state / lbm_load_state are exact for every
+ * storage type). */
 int lbm_get_populations(lbm_ctx* ctx, double* f);
 int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Exact checkpoint / resume.  The paper has no counterpart (a run of Eq. 2
+ * is a sequence of states; this saves one and continues from it).
+ * lbm_save_state copies the context's state -- the stored population
+ * deviations in the storage type and padded layout, whether they are
+ * post-collision, the step count and the status counters -- into a host
+ * buffer of lbm_state_bytes() bytes; lbm_load_state restores it into a
+ * context created with the same lattice, storage type and instance sizes
+ * (LBM_ERR_ARG otherwise; collision rule, viscosities and lid speeds may
+ * differ).  A loaded context continues bit for bit like the one saved,
+ * whatever the storage type.  Both synchronise. */
+int lbm_state_bytes(lbm_ctx* ctx, uint64_t* bytes);
+int lbm_save_state(lbm_ctx* ctx, void* host_buf);
+int lbm_load_state(lbm_ctx* ctx, const void* host_buf);
 
 /* Per-instance totals of f(x, t_n) in FP64 -- out[3*i + 0..2] = sum rho,
  * sum rho u_x, sum rho u_y -- from a deterministic two-pass reduction
@@ -220,12 +279,17 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * thread chunks, out[2] = tile height in rows, out[3] = grid size (CTAs),
  * out[4] = kernel kind (0: register-chunk kernel; 1: TMA-staged D2Q9 kernel
  * with large tiles, 2048 nodes for 2-byte storage or 1024 for FP32, on a
- * two-stage ring; 2: the same kernel with small tiles, 1024 / 512 nodes, on
- * a three-stage ring.  For kinds 1 and 2 the tile width is 64/128/256 nodes
- * chosen per instance, at most an eighth of the tile, and out[1], out[2] are
- * 0; tiles go in and out of shared memory by TMA).  Selection: the create-time
- * autotuner, or the environment variable LBM_SHAPE = "V,tw,th" (register
- * chunks), "smem" (kind 1) or "smems" (kind 2). */
+ * two-stage ring, 256 threads; 2: the same kernel with small tiles, 1024 /
+ * 512 nodes, on a three-stage ring; 3: wide CTAs of 320 threads with 2560 /
+ * 1280-node tiles on a two-stage ring.  For kinds 1 to 3 the tile width is
+ * 64/128/256 nodes chosen per instance, at most an eighth of the tile, and
+ * out[1], out[2] are 0; tiles go in and out of shared memory by TMA).  Selection: the create-time
+ * autotuner (median of three timed launches per candidate shape; the choice
+ * is cached per device, lattice, types, rule, boundary and instance sizes
+ * for the life of the process, and in the text file named by the
+ * environment variable LBM_AUTOTUNE_CACHE when set, which later processes
+ * reuse without timing), or the environment variable LBM_SHAPE = "V,tw,th"
+ * (register chunks), "smem" (kind 1), "smems" (kind 2) or "smemw" (kind 3). */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* out);
 
 /* Destroy a context (NULL-safe).  Frees library-owned memory only. */

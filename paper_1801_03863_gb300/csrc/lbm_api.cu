@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -27,45 +29,55 @@ constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even)
 size_t dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
 
 // Launch shape.  kind 0: register-chunk kernel (V nodes per thread, tiles of
-// tw x th chunks); kind 1 / 2: TMA-staged D2Q9 kernel with node pairs
-// (V = 2) and large / small tiles (smem_tile_nodes variant kind - 1), tile
-// width per instance.
+// tw x th chunks); kind 1 / 2 / 3: TMA-staged D2Q9 kernel with node pairs
+// (V = 2) in the large-tile / small-tile / wide-CTA geometry
+// (smem_tile_nodes variant kind - 1), tile width per instance.
 struct Shape {
     int V, tw, th;
     int kind = 0;
 };
-
-// Launch-shape candidates.  V (nodes per thread) is limited to the compiled
-// widths of each storage type; tw is a power of two.
-std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, int64_t max_ny) {
-    std::vector<int> vs;
-    if (storage == DT_F64) vs = {2};
-    else if (storage == DT_F32) vs = {2, 4};
-    else vs = {4, 8};
-    std::vector<Shape> out;
-    if (lattice == 2 && storage != DT_F64) {
-        out.push_back({2, 0, 0, 1});  // TMA-staged kernel, node pairs, large tiles
-        out.push_back({2, 0, 0, 2});  // TMA-staged kernel, node pairs, small tiles
-    }
-    for (int V : vs) {
-        for (int block : {128, 256}) {
-            for (int tw = 4; tw <= block; tw *= 2) {
-                const int th = block / tw;
-                if (lattice == 1 && th != 1) continue;
-                if (lattice == 2 && th > max_ny && tw < block) continue;
-                if ((int64_t)tw * V > 2 * std::max<int64_t>(max_nx, 8) && tw > 4) continue;
-                out.push_back({V, tw, th});
-            }
-        }
-    }
-    return out;
-}
 
 Shape default_shape(int lattice, int storage) {
     if (lattice == 1) return {storage == DT_F64 ? 2 : 4, 128, 1};
     if (storage == DT_F64) return {2, 16, 8};
     if (storage == DT_F32) return {4, 16, 8};
     return {8, 8, 16};
+}
+
+// Launch-shape candidates of the autotuner.  D2Q9 with FP32 arithmetic: the
+// TMA-staged kernel in both tile geometries and the default register-chunk
+// shape (which wins only on small, cache-resident lattices).  D1Q3 and the
+// FP64 path: register-chunk shapes, V = the compiled widths of the storage
+// type, tiles of 128 or 256 threads.
+std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, int64_t max_ny) {
+    std::vector<Shape> out;
+    if (lattice == 2 && storage != DT_F64) {
+        out.push_back({2, 0, 0, 1});  // TMA-staged kernel, node pairs, large tiles
+        out.push_back({2, 0, 0, 2});  // TMA-staged kernel, node pairs, small tiles
+        out.push_back({2, 0, 0, 3});  // TMA-staged kernel, node pairs, wide CTAs
+        out.push_back(default_shape(lattice, storage));
+        return out;
+    }
+    std::vector<int> vs;
+    if (storage == DT_F64) vs = {2};
+    else if (storage == DT_F32) vs = {2, 4};
+    else vs = {4, 8};
+    for (int V : vs) {
+        for (int block : {128, 256}) {
+            if (lattice == 1) {
+                if ((int64_t)block * V > 2 * std::max<int64_t>(max_nx, 8) && block > 128) continue;
+                out.push_back({V, block, 1});
+                continue;
+            }
+            for (int tw : {8, 16, 32}) {
+                const int th = block / tw;
+                if (th > max_ny && tw < 32) continue;
+                if ((int64_t)tw * V > 2 * std::max<int64_t>(max_nx, 8) && tw > 8) continue;
+                out.push_back({V, tw, th});
+            }
+        }
+    }
+    return out;
 }
 
 int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const Shape& s,
@@ -126,7 +138,8 @@ Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t
         bound += chunks * d.second / 128 + chunks / 4 + d.second + 1;
     }
     L.max_tiles = std::max({bound, count_tiles(dims, Shape{2, 0, 0, 1}, storage),
-                            count_tiles(dims, Shape{2, 0, 0, 2}, storage)});
+                            count_tiles(dims, Shape{2, 0, 0, 2}, storage),
+                            count_tiles(dims, Shape{2, 0, 0, 3}, storage)});
     return L;
 }
 
@@ -188,6 +201,7 @@ struct lbm_ctx {
     int tmaps_variant = -1;  // tile variant the TMA tensor maps were built for
     std::vector<TileDesc> tiles;
     bool initialized = false;
+    std::vector<uint8_t> inst_init;  // per-instance initial fields set (lbm_init_batch)
     bool post = false;  // stored field is post-collision
     int64_t steps = 0;
     Shape shape{};
@@ -196,6 +210,8 @@ struct lbm_ctx {
     size_t smem = 0;  // dynamic shared memory of the step kernel
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool failed = false;
+    int spin_limit = 1 << 20;  // polls of one bounded mbarrier wait in the TMA kernel
+    int lost_tile = -1;        // timeout-path test hook (LBM_TEST_LOST_TILE)
 };
 
 namespace {
@@ -277,7 +293,7 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     const void* k = nullptr;
     size_t smem = 0;
     if (s.kind >= 1) {
-        if (ctx->lattice != 2 || ctx->compute != DT_F32 || s.kind > 2) return LBM_ERR_ARG;
+        if (ctx->lattice != 2 || ctx->compute != DT_F32 || s.kind > 3) return LBM_ERR_ARG;
         const int var = s.kind - 1;
         if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, var, &smem);
         else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, var, &smem);
@@ -306,7 +322,7 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     LBM_CK(cudaMemcpyAsync(ctx->d_inst, ctx->layout.inst.data(), sizeof(InstDesc) * ctx->count,
                            cudaMemcpyHostToDevice, ctx->stream));
     LBM_CK(cudaStreamSynchronize(ctx->stream));
-    const int block = s.kind >= 1 ? 256 : s.tw * s.th;
+    const int block = s.kind >= 1 ? smem_threads(s.kind - 1) : s.tw * s.th;
     int per_sm = 0;
     LBM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     per_sm = std::max(per_sm, 1);
@@ -390,6 +406,8 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
     a.tmaps_halo = ctx->d_tmaps + (size_t)(src * 2 + 1) * ctx->count;
     a.tmaps_dst = ctx->d_tmaps + (size_t)(1 - src) * 2 * ctx->count;
     a.error = ctx->d_error;
+    a.spin_limit = ctx->spin_limit;
+    a.lost_tile = ctx->lost_tile;
     return a;
 }
 
@@ -399,7 +417,8 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
 cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
     StepArgs a = step_args(ctx, src);
     void* params[] = {&a};
-    const int block = ctx->shape.kind >= 1 ? 256 : ctx->shape.tw * ctx->shape.th;
+    const int block = ctx->shape.kind >= 1 ? smem_threads(ctx->shape.kind - 1)
+                                           : ctx->shape.tw * ctx->shape.th;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -413,37 +432,162 @@ cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
     return cudaLaunchKernelExC(&cfg, ctx->kern, params);
 }
 
-// Time candidate shapes on the zeroed (rest-state) buffers and keep the fastest.
+// Median of three timed launches of the current shape (after one untimed
+// launch) on the rest-state buffers, in milliseconds; < 0 on a CUDA error.
+float time_current_shape(lbm_ctx* ctx, cudaEvent_t* ev) {
+    if (launch_step(ctx, 0, ctx->stream) != cudaSuccess) return -1.f;
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+        if (cudaEventRecord(ev[2 * r], ctx->stream) != cudaSuccess ||
+            launch_step(ctx, (r + 1) & 1, ctx->stream) != cudaSuccess ||
+            cudaEventRecord(ev[2 * r + 1], ctx->stream) != cudaSuccess)
+            return -1.f;
+    }
+    if (cudaEventSynchronize(ev[5]) != cudaSuccess) return -1.f;
+    for (int r = 0; r < 3; ++r)
+        if (cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]) != cudaSuccess) return -1.f;
+    std::sort(t, t + 3);
+    return t[1];
+}
+
+// Autotuner cache: the chosen shape per (device, lattice, types, rule,
+// boundary, instance sizes).  Kept for the life of the process, and in the
+// text file named by LBM_AUTOTUNE_CACHE when that variable is set (one line
+// per key: "<key> V tw th kind"), so that a later process -- a profiler run,
+// for instance -- takes the same shape without timing anything.
+std::mutex g_tune_mu;
+std::map<std::string, Shape>& tune_cache() {
+    static std::map<std::string, Shape> m;
+    return m;
+}
+
+std::string tune_key(const lbm_ctx* ctx) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::string name = "?";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == ' ') c = '_';
+    // sizes as a sorted histogram, hashed (FNV-1a)
+    std::vector<std::pair<int64_t, int64_t>> d;
+    for (const InstDesc& in : ctx->layout.inst) d.push_back({in.nx, in.ny});
+    std::sort(d.begin(), d.end());
+    uint64_t h = 1469598103934665603ull;
+    for (auto& p : d)
+        for (int64_t v : {p.first, p.second}) {
+            h ^= (uint64_t)v;
+            h *= 1099511628211ull;
+        }
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s/sm%d/lat%d/st%d/cp%d/co%d/bc%d/n%d/%016llx", name.c_str(),
+             ctx->num_sms, ctx->lattice, ctx->storage, ctx->compute, ctx->collision, ctx->bc,
+             ctx->count, (unsigned long long)h);
+    return buf;
+}
+
+bool tune_lookup(const std::string& key, Shape* s) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+        *s = it->second;
+        return true;
+    }
+    const char* path = getenv("LBM_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char k[256];
+    Shape t{};
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %d %d", k, &t.V, &t.tw, &t.th, &t.kind) == 5) {
+        if (key == k) {
+            *s = t;
+            found = true;  // the last entry for a key wins
+        }
+    }
+    fclose(f);
+    if (found) tune_cache()[key] = *s;
+    return found;
+}
+
+void tune_store(const std::string& key, const Shape& s) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache()[key] = s;
+    const char* path = getenv("LBM_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d\n", key.c_str(), s.V, s.tw, s.th, s.kind);
+    fclose(f);
+}
+
+// Keep the fastest candidate shape: each is timed by the median of three
+// launches on the rest-state buffers (the collision's instruction stream does
+// not depend on the data), then the buffers and counters are cleared.  A
+// shape found in the cache is applied without timing.
 int autotune(lbm_ctx* ctx) {
+    const std::string key = tune_key(ctx);
+    Shape cached;
+    if (tune_lookup(key, &cached) && apply_shape(ctx, cached) == LBM_OK) return LBM_OK;
     std::vector<Shape> cands = candidate_shapes(ctx->lattice, ctx->storage, ctx->layout.max_nx,
                                                 ctx->layout.max_ny);
-    cudaEvent_t e0, e1;
-    LBM_CK(cudaEventCreate(&e0));
-    LBM_CK(cudaEventCreate(&e1));
+    cudaEvent_t ev[6];
+    for (int i = 0; i < 6; ++i) LBM_CK(cudaEventCreate(&ev[i]));
     float best = 1e30f;
     Shape best_s = default_shape(ctx->lattice, ctx->storage);
-    const int reps = ctx->layout.total_nodes > (1 << 22) ? 4 : 12;
+    int rc = LBM_OK;
     for (const Shape& s : cands) {
         if (apply_shape(ctx, s) != LBM_OK) continue;
-        for (int w = 0; w < 2; ++w) LBM_CK(launch_step(ctx, w & 1, ctx->stream));
-        LBM_CK(cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < reps; ++r) LBM_CK(launch_step(ctx, r & 1, ctx->stream));
-        LBM_CK(cudaEventRecord(e1, ctx->stream));
-        LBM_CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        LBM_CK(cudaEventElapsedTime(&ms, e0, e1));
+        const float ms = time_current_shape(ctx, ev);
+        if (ms < 0.f) {
+            rc = LBM_ERR_CUDA;
+            break;
+        }
         if (ms < best) {
             best = ms;
             best_s = s;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+    if (rc != LBM_OK) {
+        ctx->failed = true;
+        return rc;
+    }
     // undo the tuning steps: back to the rest state, counters cleared
     LBM_CK(cudaMemsetAsync(ctx->buf[0], 0, 2 * ctx->cv.buf_bytes, ctx->stream));
     LBM_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned long long) * 2 * ctx->count,
                            ctx->stream));
-    return apply_shape(ctx, best_s);
+    rc = apply_shape(ctx, best_s);
+    if (rc == LBM_OK) tune_store(key, best_s);
+    return rc;
+}
+
+// Capture the step loop of GRAPH_STEPS launches for both buffer parities and
+// upload the executable graphs, so that no capture or first-launch upload
+// happens inside a later lbm_step.
+int capture_graphs(lbm_ctx* ctx) {
+    for (int p = 0; p < 2; ++p) {
+        cudaGraphExec_t& g = ctx->graph[p];
+        if (g) continue;
+        cudaGraph_t graph;
+        LBM_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        int src = p;
+        for (int k = 0; k < GRAPH_STEPS; ++k) {
+            cudaError_t e = launch_step(ctx, src, ctx->capture_stream);
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(ctx->capture_stream, &graph);
+                LBM_CK(e);
+            }
+            src = 1 - src;
+        }
+        LBM_CK(cudaStreamEndCapture(ctx->capture_stream, &graph));
+        cudaError_t e = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        LBM_CK(e);
+        LBM_CK(cudaGraphUpload(g, ctx->stream));
+    }
+    return LBM_OK;
 }
 
 bool parse_shape_env(Shape* s) {
@@ -455,6 +599,10 @@ bool parse_shape_env(Shape* s) {
     }
     if (strcmp(e, "smems") == 0) {
         *s = {2, 0, 0, 2};
+        return true;
+    }
+    if (strcmp(e, "smemw") == 0) {
+        *s = {2, 0, 0, 3};
         return true;
     }
     int v, tw, th;
@@ -497,6 +645,89 @@ int validate_dims(int lat, int32_t count, const int64_t* dims,
         out->push_back({nx, ny});
     }
     return LBM_OK;
+}
+
+// Device address of a host array the GPU can read and write in place
+// (page-locked memory registered with CUDA: cudaHostAlloc, cudaHostRegister,
+// torch's pin_memory), or nullptr.  A null array counts as addressable.
+// Host I/O with such arrays runs its kernels straight on them, without
+// staging copies: on a GB300 the kernel streams them over the CPU-GPU link.
+template <typename P> bool device_view(P* host, P** dev) {
+    if (!host) {
+        *dev = nullptr;
+        return true;
+    }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+    *dev = static_cast<P*>(at.devicePointer);
+    return true;
+}
+
+// Auxiliary-kernel arguments that cover instance i alone, with host arrays
+// indexed from its first node.
+AuxArgs aux_args_instance(const lbm_ctx* ctx, int i) {
+    AuxArgs a = aux_args(ctx);
+    const InstDesc& in = ctx->layout.inst[i];
+    a.inst = ctx->d_inst + i;
+    a.count = 1;
+    a.max_nodes = (int64_t)in.nx * in.ny;
+    a.node_base = in.node0;
+    return a;
+}
+
+// Header of a saved state (lbm_save_state): the layout it fits and the
+// context's position in its run, followed by the status counters and the
+// raw population buffer.
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t lattice, storage, count;
+    int32_t post, reserved;
+    int64_t steps;
+    uint64_t layout_hash, buf_bytes, status_bytes;
+    uint64_t pad[8];
+};
+static_assert(sizeof(StateHeader) == 128, "state header is 128 bytes");
+constexpr char STATE_MAGIC[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+
+uint64_t layout_hash(const lbm_ctx* ctx) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        h ^= v;
+        h *= 1099511628211ull;
+    };
+    mix((uint64_t)ctx->lattice);
+    mix((uint64_t)ctx->storage);
+    for (const InstDesc& in : ctx->layout.inst) {
+        mix((uint64_t)in.nx);
+        mix((uint64_t)in.ny);
+        mix((uint64_t)in.pitch);
+        mix((uint64_t)in.plane);
+        mix((uint64_t)in.off);
+    }
+    return h;
+}
+
+// LBM_ERR_UNSTABLE when instance i has flagged an unstable node (sticky
+// error word first); syncs.
+int instance_status(lbm_ctx* ctx, int32_t instance) {
+    int64_t c[3];
+    int rc = lbm_status_instance(ctx, instance, c);
+    if (rc != LBM_OK) return rc;
+    unsigned int err = 0;
+    LBM_CK(cudaMemcpyAsync(&err, ctx->d_error, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    if (err) return LBM_ERR_TIMEOUT;
+    return c[1] ? LBM_ERR_UNSTABLE : LBM_OK;
+}
+
+uint64_t state_bytes(const lbm_ctx* ctx) {
+    return sizeof(StateHeader) + sizeof(unsigned long long) * 2 * (uint64_t)ctx->count +
+           (uint64_t)ctx->cv.buf_bytes;
 }
 
 }  // namespace
@@ -582,6 +813,13 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
     ctx->rho0 = o.rho0;
     ctx->stream = static_cast<cudaStream_t>(o.stream);
     ctx->num_sms = prop.multiProcessorCount;
+    // Test hooks of the bounded-wait timeout path (TMA kernel): a smaller
+    // spin limit, and one tile whose copies are never issued.
+    if (const char* e = getenv("LBM_SPIN_LIMIT")) {
+        const long v = strtol(e, nullptr, 10);
+        if (v >= 1 && v <= (1 << 20)) ctx->spin_limit = (int)v;
+    }
+    if (const char* e = getenv("LBM_TEST_LOST_TILE")) ctx->lost_tile = (int)strtol(e, nullptr, 10);
     ctx->layout = make_layout(lat, o.storage, d);
     ctx->cv = carve(ctx->layout, lat, o.storage, count);
     for (int i = 0; i < count; ++i) {
@@ -656,6 +894,8 @@ int lbm_create_batch(lbm_ctx** out, lbm_lattice lat, int32_t count, const int64_
     else if (o.autotune && !getenv("LBM_NO_AUTOTUNE")) rc = autotune(ctx);
     else rc = apply_shape(ctx, default_shape(lat, o.storage));
     if (rc != LBM_OK) return fail(rc);
+    rc = capture_graphs(ctx);
+    if (rc != LBM_OK) return fail(rc);
     *out = ctx;
     return LBM_OK;
 }
@@ -689,6 +929,7 @@ int lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, const dou
     LBM_CK(cudaMemsetAsync(ctx->d_error, 0, sizeof(unsigned int), ctx->stream));
     ctx->post = false;
     ctx->initialized = true;
+    ctx->inst_init.assign(ctx->count, 1);
     ctx->steps = 0;
     return LBM_OK;
 }
@@ -696,6 +937,14 @@ int lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, const dou
 int lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy) {
     if (!ctx || !rho) return LBM_ERR_ARG;
     if (ctx->failed) return LBM_ERR_CUDA;
+    const double *dr, *dx, *dy;
+    if (device_view(rho, &dr) && device_view(ux, &dx) && device_view(uy, &dy)) {
+        // page-locked arrays: the init kernel reads them in place
+        int rc = lbm_init_device(ctx, dr, dx, ctx->Q == 9 ? dy : nullptr);
+        if (rc != LBM_OK) return rc;
+        LBM_CK(cudaStreamSynchronize(ctx->stream));
+        return LBM_OK;
+    }
     const size_t n = (size_t)ctx->layout.total_nodes;
     double* r = ctx->d_stage;
     double* x = ux ? ctx->d_stage + n : nullptr;
@@ -727,21 +976,8 @@ int lbm_step(lbm_ctx* ctx, int64_t n) {
     while (n >= GRAPH_STEPS) {
         cudaGraphExec_t& g = ctx->graph[ctx->cur];
         if (!g) {
-            cudaGraph_t graph;
-            LBM_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-            int src = ctx->cur;
-            for (int k = 0; k < GRAPH_STEPS; ++k) {
-                cudaError_t e = launch_step(ctx, src, ctx->capture_stream);
-                if (e != cudaSuccess) {
-                    cudaStreamEndCapture(ctx->capture_stream, &graph);
-                    LBM_CK(e);
-                }
-                src = 1 - src;
-            }
-            LBM_CK(cudaStreamEndCapture(ctx->capture_stream, &graph));
-            cudaError_t e = cudaGraphInstantiate(&g, graph, 0);
-            cudaGraphDestroy(graph);
-            LBM_CK(e);
+            const int rc = capture_graphs(ctx);
+            if (rc != LBM_OK) return rc;
         }
         LBM_CK(cudaGraphLaunch(g, ctx->stream));
         n -= GRAPH_STEPS;
@@ -828,17 +1064,26 @@ int lbm_status(lbm_ctx* ctx, int64_t* counters) {
 
 int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy) {
     if (!ctx || !rho) return LBM_ERR_ARG;
-    const size_t n = (size_t)ctx->layout.total_nodes;
-    double* r = ctx->d_stage;
-    double* x = ctx->d_stage + n;
-    double* y = ctx->d_stage + 2 * n;
-    int rc = lbm_moments_device(ctx, r, x, y);
-    if (rc != LBM_OK) return rc;
-    LBM_CK(cudaMemcpyAsync(rho, r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    if (ux) LBM_CK(cudaMemcpyAsync(ux, x, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    if (uy && ctx->Q == 9)
-        LBM_CK(cudaMemcpyAsync(uy, y, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    double *hr, *hx, *hy;
+    if (device_view(rho, &hr) && device_view(ux, &hx) && device_view(uy, &hy)) {
+        // page-locked arrays: the moments kernel writes them in place
+        int rc = lbm_moments_device(ctx, hr, hx, hy);
+        if (rc != LBM_OK) return rc;
+    } else {
+        const size_t n = (size_t)ctx->layout.total_nodes;
+        double* r = ctx->d_stage;
+        double* x = ctx->d_stage + n;
+        double* y = ctx->d_stage + 2 * n;
+        int rc = lbm_moments_device(ctx, r, x, y);
+        if (rc != LBM_OK) return rc;
+        LBM_CK(cudaMemcpyAsync(rho, r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (ux)
+            LBM_CK(cudaMemcpyAsync(ux, x, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (uy && ctx->Q == 9)
+            LBM_CK(cudaMemcpyAsync(uy, y, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
     LBM_CK(cudaStreamSynchronize(ctx->stream));
+    int rc;
     int64_t c[3];
     rc = lbm_status(ctx, c);
     if (rc != LBM_OK) return rc;
@@ -871,6 +1116,7 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f) {
     LBM_CK(cudaStreamSynchronize(ctx->stream));
     ctx->post = false;
     ctx->initialized = true;
+    ctx->inst_init.assign(ctx->count, 1);
     return LBM_OK;
 }
 
@@ -894,6 +1140,138 @@ int lbm_conservation_device(lbm_ctx* ctx, double* out) {
     AuxArgs a = aux_args(ctx);
     LBM_CK(run_aux(AuxOp::Conservation, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr,
                    out, ctx->d_partials, nullptr));
+    return LBM_OK;
+}
+
+int lbm_init_batch(lbm_ctx* ctx, int32_t instance, const double* rho, const double* ux,
+                   const double* uy) {
+    if (!ctx || !rho || instance < 0 || instance >= ctx->count) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (ctx->post) return LBM_ERR_STATE;  // mid-run: the stored field is post-collision
+    const InstDesc& in = ctx->layout.inst[instance];
+    const size_t n = (size_t)in.nx * in.ny;
+    double* r = ctx->d_stage;
+    double* x = ux ? ctx->d_stage + n : nullptr;
+    double* y = (uy && ctx->Q == 9) ? ctx->d_stage + 2 * n : nullptr;
+    LBM_CK(cudaMemcpyAsync(r, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (x) LBM_CK(cudaMemcpyAsync(x, ux, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (y) LBM_CK(cudaMemcpyAsync(y, uy, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    AuxArgs a = aux_args_instance(ctx, instance);
+    LBM_CK(run_aux(AuxOp::Init, a, nullptr, ctx->buf[ctx->cur], r, x, y, nullptr, nullptr,
+                   nullptr));
+    LBM_CK(cudaMemsetAsync(ctx->d_status + 2 * instance, 0, 2 * sizeof(unsigned long long),
+                           ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->inst_init.size() != (size_t)ctx->count) ctx->inst_init.assign(ctx->count, 0);
+    ctx->inst_init[instance] = 1;
+    if (!ctx->initialized &&
+        std::all_of(ctx->inst_init.begin(), ctx->inst_init.end(), [](uint8_t v) { return v; })) {
+        LBM_CK(cudaMemsetAsync(ctx->d_error, 0, sizeof(unsigned int), ctx->stream));
+        LBM_CK(cudaStreamSynchronize(ctx->stream));
+        ctx->initialized = true;
+        ctx->steps = 0;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments_batch_device(lbm_ctx* ctx, int32_t instance, double* rho, double* ux, double* uy) {
+    if (!ctx || !rho || instance < 0 || instance >= ctx->count) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    AuxArgs a = aux_args_instance(ctx, instance);
+    LBM_CK(run_aux(AuxOp::Moments, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr, rho,
+                   ux, ctx->Q == 9 ? uy : nullptr));
+    return LBM_OK;
+}
+
+int lbm_moments_batch(lbm_ctx* ctx, int32_t instance, double* rho, double* ux, double* uy) {
+    if (!ctx || !rho || instance < 0 || instance >= ctx->count) return LBM_ERR_ARG;
+    const InstDesc& in = ctx->layout.inst[instance];
+    const size_t n = (size_t)in.nx * in.ny;
+    double* r = ctx->d_stage;
+    double* x = ctx->d_stage + n;
+    double* y = ctx->d_stage + 2 * n;
+    int rc = lbm_moments_batch_device(ctx, instance, r, x, y);
+    if (rc != LBM_OK) return rc;
+    LBM_CK(cudaMemcpyAsync(rho, r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ux) LBM_CK(cudaMemcpyAsync(ux, x, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (uy && ctx->Q == 9)
+        LBM_CK(cudaMemcpyAsync(uy, y, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return instance_status(ctx, instance);
+}
+
+int lbm_stream_function_batch(lbm_ctx* ctx, int32_t instance, double* psi) {
+    if (!ctx || !psi || instance < 0 || instance >= ctx->count) return LBM_ERR_ARG;
+    if (ctx->Q != 9) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    const InstDesc& in = ctx->layout.inst[instance];
+    const size_t n = (size_t)in.nx * in.ny;
+    AuxArgs a = aux_args_instance(ctx, instance);
+    LBM_CK(run_aux(AuxOp::Moments, a, ctx->buf[ctx->cur], nullptr, nullptr, nullptr, nullptr,
+                   ctx->d_stage, ctx->d_stage + n, ctx->d_stage + 2 * n));
+    LBM_CK(stream_function(a, in.ny, ctx->d_stage + 2 * n, ctx->d_stage + 3 * n));
+    LBM_CK(cudaMemcpyAsync(psi, ctx->d_stage + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return instance_status(ctx, instance);
+}
+
+int lbm_state_bytes(lbm_ctx* ctx, uint64_t* bytes) {
+    if (!ctx || !bytes) return LBM_ERR_ARG;
+    *bytes = state_bytes(ctx);
+    return LBM_OK;
+}
+
+int lbm_save_state(lbm_ctx* ctx, void* host_buf) {
+    if (!ctx || !host_buf) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, STATE_MAGIC, sizeof h.magic);
+    h.version = 1;
+    h.lattice = ctx->lattice;
+    h.storage = ctx->storage;
+    h.count = ctx->count;
+    h.post = ctx->post ? 1 : 0;
+    h.steps = ctx->steps;
+    h.layout_hash = layout_hash(ctx);
+    h.status_bytes = sizeof(unsigned long long) * 2 * (uint64_t)ctx->count;
+    h.buf_bytes = ctx->cv.buf_bytes;
+    char* out = static_cast<char*>(host_buf);
+    std::memcpy(out, &h, sizeof h);
+    LBM_CK(cudaMemcpyAsync(out + sizeof h, ctx->d_status, h.status_bytes, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    LBM_CK(cudaMemcpyAsync(out + sizeof h + h.status_bytes, ctx->buf[ctx->cur], h.buf_bytes,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_ctx* ctx, const void* host_buf) {
+    if (!ctx || !host_buf) return LBM_ERR_ARG;
+    if (ctx->failed) return LBM_ERR_CUDA;
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    if (std::memcmp(h.magic, STATE_MAGIC, sizeof h.magic) != 0 || h.version != 1 ||
+        h.lattice != ctx->lattice || h.storage != ctx->storage || h.count != ctx->count ||
+        h.layout_hash != layout_hash(ctx) || h.buf_bytes != ctx->cv.buf_bytes ||
+        h.status_bytes != sizeof(unsigned long long) * 2 * (uint64_t)ctx->count)
+        return LBM_ERR_ARG;
+    const char* in = static_cast<const char*>(host_buf);
+    LBM_CK(cudaMemcpyAsync(ctx->d_status, in + sizeof h, h.status_bytes, cudaMemcpyHostToDevice,
+                           ctx->stream));
+    LBM_CK(cudaMemcpyAsync(ctx->buf[0], in + sizeof h + h.status_bytes, h.buf_bytes,
+                           cudaMemcpyHostToDevice, ctx->stream));
+    LBM_CK(cudaMemsetAsync(ctx->d_error, 0, sizeof(unsigned int), ctx->stream));
+    LBM_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->cur = 0;
+    ctx->post = h.post != 0;
+    ctx->steps = h.steps;
+    ctx->initialized = true;
+    ctx->inst_init.assign(ctx->count, 1);
     return LBM_OK;
 }
 

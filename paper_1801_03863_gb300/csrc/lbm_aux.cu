@@ -43,26 +43,47 @@ __device__ void node_state(const S* base, const InstDesc& in, int x, int y, bool
     }
 }
 
-// f^eq(rho, u) - W rho0 in FP64 (Eq. numerical-plyeqm).
+// f^eq(rho, u) - W rho0 in FP64 (Eq. numerical-plyeqm):
+//   W_a (rho - rho0) + W_a rho (3 v.u + 9/2 (v.u)^2 - 3/2 u^2),
+// with the even and odd parts in v shared by opposite velocities.
 template <class Lat>
 __device__ void eq_dev(double rho, double ux, double uy, double rho0, double (&d)[Lat::Q]) {
-    const double uu = ux * ux + uy * uy;
+    const double dr = rho - rho0;
+    const double b0 = -1.5 * (ux * ux + uy * uy);
 #pragma unroll
     for (int a = 0; a < Lat::Q; ++a) {
+        const int o = Lat::opp(a);
+        if (o < a) continue;  // filled with its opposite
+        const double w = Lat::w(a), wr = w * rho;
         const double vu = Lat::vx(a) * ux + Lat::vy(a) * uy;
-        d[a] = Lat::w(a) * (rho - rho0) + Lat::w(a) * rho * (3.0 * vu + 4.5 * vu * vu - 1.5 * uu);
+        const double even = fma(4.5 * vu, vu, b0);
+        const double odd = 3.0 * vu;
+        const double base = fma(wr, even, w * dr);
+        d[a] = fma(wr, odd, base);
+        if (o != a) d[o] = fma(-wr, odd, base);
     }
 }
 
+// Node k of instance `in` (row-major, x fastest) as (x, y): 32-bit index
+// arithmetic (nx * ny < 2^31 for every instance).
+__device__ __forceinline__ void node_xy(uint32_t k, uint32_t nx, int& x, int& y) {
+    const uint32_t yy = k / nx;
+    y = (int)yy;
+    x = (int)(k - yy * nx);
+}
+
+// Host arrays are indexed from the first node of the instances the launch
+// covers: node0 - node_base (node_base = 0 for whole-context calls, the
+// instance's node0 for single-instance calls).
 template <class Lat, typename S>
 __global__ void init_kernel(S* dst, const InstDesc* insts, const double* rho, const double* ux,
-                            const double* uy, double rho0) {
+                            const double* uy, double rho0, int64_t node_base) {
     const InstDesc in = insts[blockIdx.y];
-    const int64_t n = (int64_t)in.nx * in.ny;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
-        const int64_t g = in.node0 + k;
+    const uint32_t n = (uint32_t)in.nx * (uint32_t)in.ny;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int x, y;
+        node_xy(k, (uint32_t)in.nx, x, y);
+        const int64_t g = in.node0 - node_base + k;
         double d[Lat::Q];
         eq_dev<Lat>(rho[g], ux ? ux[g] : 0.0, (uy && Lat::Q == 9) ? uy[g] : 0.0, rho0, d);
 #pragma unroll
@@ -74,10 +95,10 @@ __global__ void init_kernel(S* dst, const InstDesc* insts, const double* rho, co
 template <class Lat, typename S>
 __global__ void set_f_kernel(S* dst, const InstDesc* insts, const double* f, double rho0) {
     const InstDesc in = insts[blockIdx.y];
-    const int64_t n = (int64_t)in.nx * in.ny;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+    const uint32_t n = (uint32_t)in.nx * (uint32_t)in.ny;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int x, y;
+        node_xy(k, (uint32_t)in.nx, x, y);
 #pragma unroll
         for (int a = 0; a < Lat::Q; ++a) {
             const double fa = f[in.node0 * Lat::Q + (int64_t)a * n + k];
@@ -88,51 +109,72 @@ __global__ void set_f_kernel(S* dst, const InstDesc* insts, const double* f, dou
 }
 
 // First step after a state was loaded: collide in place, no streaming
-// (the loaded field is f(x, t_n) itself, Eq. 2's collision input).
+// (the loaded field is f(x, t_n) itself, Eq. 2's collision input).  The
+// arithmetic is that of the step kernels -- FP64, or node pairs in packed
+// FP32x2 for FP32 -- with the same rates and boundary rules, so this step
+// rounds exactly like a step kernel colliding the same pulled values: a
+// state saved from a running context and loaded into a new one continues
+// bit for bit.  One thread per node pair (x, x + 1) of a row; at an odd
+// width the second lane repeats the last node and is discarded.
 template <class Lat, typename S, typename T, int COLL>
 __global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* insts, double rho0,
                                        unsigned long long* status) {
-    using CT = typename std::conditional<std::is_same<T, float>::value, F1, T>::type;
+    using CT = typename std::conditional<std::is_same<T, float>::value, F2, T>::type;
+    using N = Num<CT>;
+    using LT = typename LaneOf<CT>::type;
+    constexpr int P = N::LANES;
     const int inst = blockIdx.y;
     const InstDesc& in = insts[inst];
-    const int64_t n = (int64_t)in.nx * in.ny;
+    const uint32_t groups = ((uint32_t)in.nx + P - 1) / P;  // node groups per row
+    const uint32_t n = groups * (uint32_t)in.ny;
+    const Rates<CT> rates{CT((LT)in.omega), CT((LT)in.omega2), CT((LT)in.s_e), CT((LT)in.s_eps)};
+    const CT rho0v = CT((LT)rho0);
     unsigned long long n_skip = 0, n_unst = 0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int g, y;
+        node_xy(k, groups, g, y);
+        const int x0 = g * P;
         CT d[Lat::Q], o[Lat::Q];
 #pragma unroll
         for (int a = 0; a < Lat::Q; ++a) {
-            const S v = *elem_ptr<Lat, S>(src, in, a, x, y);
-            if constexpr (std::is_same<T, double>::value) d[a] = Store<S>::to_f64(v);
-            else d[a] = CT(Store<S>::to_f32(v));
-        }
-        const Rates<CT> rates{CT((T)in.omega), CT((T)in.omega2), CT((T)in.s_e), CT((T)in.s_eps)};
-        uint32_t st = Collide<Lat, COLL, CT>::run(d, CT((T)rho0), rates, o);
-        if (in.bc == BC_CAVITY) {
-            const bool wall = (x == 0) || (x == in.nx - 1) || (y == 0);
-            const bool lid = !wall && (y == in.ny - 1);
-            if (wall) {
 #pragma unroll
-                for (int a = 0; a < Lat::Q; ++a) o[a] = d[Lat::opp(a)];
-                st = 0;
-            } else if (lid) {
-#pragma unroll
-                for (int a = 0; a < Lat::Q; ++a) {
-                    if constexpr (std::is_same<T, double>::value) o[a] = in.lid_dev[a];
-                    else o[a] = CT(in.lid_dev_f[a]);
-                }
-                st = 0;
+            for (int l = 0; l < P; ++l) {
+                const int x = min(x0 + l, in.nx - 1);
+                const S v = *elem_ptr<Lat, S>(src, in, a, x, y);
+                if constexpr (std::is_same<T, double>::value) d[a] = Store<S>::to_f64(v);
+                else N::set_lane(d[a], l, Store<S>::to_f32(v));
             }
         }
-        n_skip += st & ST_NEWTON_SKIPPED;
-        n_unst += (st & ST_UNSTABLE) >> 1;
+        uint32_t st = Collide<Lat, COLL, CT, (int)sizeof(S)>::run(d, rho0v, rates, o);
+        if (in.bc == BC_CAVITY) {
 #pragma unroll
-        for (int a = 0; a < Lat::Q; ++a) {
-            if constexpr (std::is_same<T, double>::value)
-                dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(o[a]);
-            else
-                dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x] = Store<S>::from(o[a].v);
+            for (int l = 0; l < P; ++l) {
+                const int x = x0 + l;
+                const bool wall = (x == 0) || (x == in.nx - 1) || (y == 0);
+                const bool lid = !wall && (y == in.ny - 1);
+                if (wall) {
+#pragma unroll
+                    for (int a = 0; a < Lat::Q; ++a) N::set_lane(o[a], l, N::lane(d[Lat::opp(a)], l));
+                    st &= ~(3u << (2 * l));
+                } else if (lid) {
+#pragma unroll
+                    for (int a = 0; a < Lat::Q; ++a) {
+                        if constexpr (std::is_same<T, double>::value) N::set_lane(o[a], l, in.lid_dev[a]);
+                        else N::set_lane(o[a], l, in.lid_dev_f[a]);
+                    }
+                    st &= ~(3u << (2 * l));
+                }
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            if (x0 + l >= in.nx) continue;
+            n_skip += (st >> (2 * l)) & ST_NEWTON_SKIPPED;
+            n_unst += ((st >> (2 * l)) & ST_UNSTABLE) >> 1;
+#pragma unroll
+            for (int a = 0; a < Lat::Q; ++a)
+                dst[in.off + (int64_t)a * in.plane + (int64_t)y * in.pitch + x0 + l] =
+                    Store<S>::from(N::lane(o[a], l));
         }
     }
     if (n_skip) atomicAdd(status + 2 * inst + 0, n_skip);
@@ -141,12 +183,12 @@ __global__ void collide_inplace_kernel(const S* src, S* dst, const InstDesc* ins
 
 template <class Lat, typename S>
 __global__ void moments_kernel(const S* src, const InstDesc* insts, bool pulled, double rho0,
-                               double* rho, double* ux, double* uy) {
+                               double* rho, double* ux, double* uy, int64_t node_base) {
     const InstDesc in = insts[blockIdx.y];
-    const int64_t n = (int64_t)in.nx * in.ny;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+    const uint32_t n = (uint32_t)in.nx * (uint32_t)in.ny;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int x, y;
+        node_xy(k, (uint32_t)in.nx, x, y);
         double d[Lat::Q];
         node_state<Lat, S>(src, in, x, y, pulled, d);
         double dr = 0.0, jx = 0.0, jy = 0.0;
@@ -157,10 +199,11 @@ __global__ void moments_kernel(const S* src, const InstDesc* insts, bool pulled,
             jy += Lat::vy(a) * d[a];
         }
         const double r = rho0 + dr;
-        const int64_t g = in.node0 + k;
+        const double ir = 1.0 / r;
+        const int64_t g = in.node0 - node_base + k;
         rho[g] = r;
-        if (ux) ux[g] = jx / r;
-        if (uy) uy[g] = jy / r;
+        if (ux) ux[g] = jx * ir;
+        if (uy) uy[g] = jy * ir;
     }
 }
 
@@ -168,10 +211,10 @@ template <class Lat, typename S>
 __global__ void gather_f_kernel(const S* src, const InstDesc* insts, bool pulled, double rho0,
                                 double* f) {
     const InstDesc in = insts[blockIdx.y];
-    const int64_t n = (int64_t)in.nx * in.ny;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(k % in.nx), y = (int)(k / in.nx);
+    const uint32_t n = (uint32_t)in.nx * (uint32_t)in.ny;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int x, y;
+        node_xy(k, (uint32_t)in.nx, x, y);
         double d[Lat::Q];
         node_state<Lat, S>(src, in, x, y, pulled, d);
 #pragma unroll
@@ -209,12 +252,13 @@ __device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, 
 // (P_i = cons_partials(ny_i)); thread t takes x = t, t + CONS_THREADS, ...
 // of each of those rows, rows in increasing order, and the block reduces
 // its threads in a fixed tree into partials[(i*CONS_PARTIALS + b)*3 + c].
-// The order is fixed by the instance alone.  Every sum runs in FP64, except
-// the node-level sums of 2-byte storage, which add the nine 11- or
-// 8-bit-significand deviations in FP32 (error below 9 * 2^-24 * sum |d|,
-// far under the storage rounding itself) before the FP64 sums across
-// nodes.  Interior nodes pull with plain shifted loads; the outer ring
-// applies the boundary rules.
+// The order is fixed by the instance alone.  The sums across nodes run in
+// FP64, and so do the node sums of every storage type except FP16, whose
+// node sums are exact integers instead: every FP16 value is a multiple of
+// 2^-24 below 2^16 in magnitude, so 2^24 d is an integer below 2^40 and nine
+// of them add exactly in 64-bit integers (a non-finite value takes the FP64
+// path, so that it propagates).  Interior nodes pull with plain shifted
+// loads; the outer ring applies the boundary rules.
 template <class Lat, typename S>
 __global__ void __launch_bounds__(CONS_THREADS)
 cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool pulled,
@@ -243,24 +287,34 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
             } else {
                 node_state<Lat, S>(src, in, x, y, pulled, d);
             }
-            if constexpr (sizeof(S) >= 4) {
+            bool exact = false;
+            if constexpr (std::is_same<S, __half>::value) {
+                long long r0 = 0, r1 = 0, r2 = 0;
+                bool finite = true;
 #pragma unroll
                 for (int a = 0; a < Lat::Q; ++a) {
-                    s0 += d[a];
-                    if (Lat::vx(a) != 0) s1 += Lat::vx(a) * d[a];
-                    if (Lat::vy(a) != 0) s2 += Lat::vy(a) * d[a];
+                    finite = finite && (fabsf(d[a]) <= 65504.f);
+                    const long long v = __float2ll_rn(d[a] * 16777216.f);  // 2^24 d, exact
+                    r0 += v;
+                    if (Lat::vx(a) != 0) r1 += Lat::vx(a) > 0 ? v : -v;
+                    if (Lat::vy(a) != 0) r2 += Lat::vy(a) > 0 ? v : -v;
                 }
-            } else {
-                float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+                if (finite) {
+                    constexpr double inv = 1.0 / 16777216.0;
+                    s0 += (double)r0 * inv;
+                    s1 += (double)r1 * inv;
+                    s2 += (double)r2 * inv;
+                    exact = true;
+                }
+            }
+            if (!exact) {
 #pragma unroll
                 for (int a = 0; a < Lat::Q; ++a) {
-                    r0 += d[a];
-                    if (Lat::vx(a) != 0) r1 += (float)Lat::vx(a) * d[a];
-                    if (Lat::vy(a) != 0) r2 += (float)Lat::vy(a) * d[a];
+                    const double v = (double)d[a];
+                    s0 += v;
+                    if (Lat::vx(a) != 0) s1 += Lat::vx(a) * v;
+                    if (Lat::vy(a) != 0) s2 += Lat::vy(a) * v;
                 }
-                s0 += (double)r0;
-                s1 += (double)r1;
-                s2 += (double)r2;
             }
         }
     }
@@ -333,7 +387,7 @@ cudaError_t aux_dispatch(AuxOp op, const AuxArgs& a, const void* src, void* dst,
     switch (op) {
         case AuxOp::Init:
             init_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<S*>(dst), a.inst, p0, p1,
-                                                                 p2, a.rho0);
+                                                                 p2, a.rho0, a.node_base);
             break;
         case AuxOp::SetF:
             set_f_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<S*>(dst), a.inst, p0,
@@ -341,7 +395,8 @@ cudaError_t aux_dispatch(AuxOp op, const AuxArgs& a, const void* src, void* dst,
             break;
         case AuxOp::Moments:
             moments_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<const S*>(src), a.inst,
-                                                                    a.pulled, a.rho0, o0, o1, o2);
+                                                                    a.pulled, a.rho0, o0, o1, o2,
+                                                                    a.node_base);
             break;
         case AuxOp::GatherF:
             gather_f_kernel<Lat, S><<<g, AUX_THREADS, 0, a.stream>>>(static_cast<const S*>(src),
@@ -386,12 +441,13 @@ cudaError_t aux_by_storage(AuxOp op, const AuxArgs& a, const void* src, void* ds
 // wall and the trapezoidal rule on the last interval when x is odd.  One
 // thread per row (rows of instance blockIdx.y).
 __global__ void stream_function_kernel(const double* __restrict__ uy,
-                                       const InstDesc* __restrict__ insts, double* __restrict__ psi) {
+                                       const InstDesc* __restrict__ insts, double* __restrict__ psi,
+                                       int64_t node_base) {
     const InstDesc& in = insts[blockIdx.y];
     const int nx = in.nx;
     for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < in.ny; y += gridDim.x * blockDim.x) {
-        const double* u = uy + in.node0 + (int64_t)y * nx;
-        double* p = psi + in.node0 + (int64_t)y * nx;
+        const double* u = uy + (in.node0 - node_base) + (int64_t)y * nx;
+        double* p = psi + (in.node0 - node_base) + (int64_t)y * nx;
         double simpson = 0.0;  // integral over [0, x] at the last even x
         p[0] = 0.0;
         for (int x = 1; x < nx; ++x) {
@@ -417,7 +473,7 @@ cudaError_t stream_function(const AuxArgs& a, int64_t max_ny, const double* uy, 
     const int threads = 128;
     const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_ny + threads - 1) / threads, 1024)),
                     (unsigned)a.count);
-    stream_function_kernel<<<grid, threads, 0, a.stream>>>(uy, a.inst, psi);
+    stream_function_kernel<<<grid, threads, 0, a.stream>>>(uy, a.inst, psi, a.node_base);
     return cudaGetLastError();
 }
 

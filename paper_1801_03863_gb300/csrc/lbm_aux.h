@@ -31,6 +31,8 @@ struct AuxArgs {
     cudaStream_t stream;
     const int2* cons_items;  // device: (instance, partial) of each conservation block
     int32_t cons_nitems;
+    int64_t node_base = 0;   // host-array index of the first node the call covers (Init,
+                             // Moments, stream_function): arrays start at that node
 };
 
 // Init:           dst <- f^eq(rho=p0, ux=p1, uy=p2) deviations
@@ -74,19 +76,33 @@ const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes
 #ifndef LBM_SMEM_TILE4_SMALL
 #define LBM_SMEM_TILE4_SMALL 512
 #endif
-// Nodes per tile of the TMA-staged kernel: variant 0 = large tiles (fewer
-// per-tile costs, for arithmetic-bound rules), 1 = small tiles with a deeper
-// ring (more copies in flight, for bandwidth-bound rules).
+#ifndef LBM_SMEM_TILE2_WIDE
+#define LBM_SMEM_TILE2_WIDE 2560
+#endif
+#ifndef LBM_SMEM_TILE4_WIDE
+#define LBM_SMEM_TILE4_WIDE 1280
+#endif
+// Geometries of the TMA-staged kernel (variant = launch-shape kind - 1):
+//   0  large tiles: 2048 nodes (2-byte storage) / 1024 (FP32), 256 threads,
+//      two-stage ring (fewer per-tile costs, for arithmetic-bound rules);
+//   1  small tiles: 1024 / 512 nodes, 256 threads, three-stage ring (more
+//      copies in flight, for bandwidth-bound rules);
+//   2  wide CTAs: 2560 / 1280 nodes, 320 threads (ten warps), two-stage
+//      ring: two CTAs give 20 warps per SM instead of 16, at a register
+//      budget of 102 per thread.
 inline int smem_tile_nodes(int storage, int variant) {
     if (variant == 1) return storage == 1 ? LBM_SMEM_TILE4_SMALL : LBM_SMEM_TILE2_SMALL;
+    if (variant == 2) return storage == 1 ? LBM_SMEM_TILE4_WIDE : LBM_SMEM_TILE2_WIDE;
     return storage == 1 ? LBM_SMEM_TILE4 : LBM_SMEM_TILE2;
 }
+inline int smem_threads(int variant) { return variant == 2 ? 320 : 256; }
 // Tile width: 64, 128 or 256 nodes by the instance width, at most
-// tile_nodes / 8, so that each warp's units (tile_nodes / 512 rows of 64
-// nodes) cover whole tile rows.
+// tile_nodes / 8, so that each warp's units (tile_nodes / (2 * threads)
+// units of 64 nodes) cover whole tile rows.
 inline int smem_tile_width(int64_t nx, int tile_nodes) {
-    const int w = nx >= 256 ? 256 : (nx >= 128 ? 128 : 64);
-    return w < tile_nodes / 8 ? w : tile_nodes / 8;
+    int w = nx >= 256 ? 256 : (nx >= 128 ? 128 : 64);
+    while (w > 64 && w > tile_nodes / 8) w /= 2;
+    return w;
 }
 
 }  // namespace lbm

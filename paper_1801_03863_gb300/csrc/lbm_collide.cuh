@@ -18,7 +18,8 @@
 // (the "+1" drops out because sum_a T_ka = 0 for every free row k), and
 //     p^post_a = p^start_a - sum_k T_ka s~_k.
 // A and b have small integer coefficients, so the 4x4 system is assembled in
-// about 40 additions.  The start point p^start = T^-1 M^start (constraints
+// about 30 additions; it is solved for D s~ with D = diag(1, 2, 2, 2), whose
+// matrix D^-1 A D^-1 drops the common factors of the eps, q_x, q_y rows.  The start point p^start = T^-1 M^start (constraints
 // imposed, free moments at their equilibrium values) equals the polynomial
 // equilibrium plus the BGK-relaxed non-equilibrium stress:
 //     p^start_a = W_a [1 + delta_a],
@@ -172,9 +173,40 @@ __device__ __forceinline__ void spd4_solve(T a11, T a21, T a22, T a31, T a32, T 
     x1 = N::mad(-l41, x4, N::mad(-l31, x3, N::mad(-l21, x2, b1 * r1)));
 }
 
+#ifndef LBM_MX4_LOGP
+#define LBM_MX4_LOGP 1  // FP32 MinxEnt4: logarithms of pair products / quotients (7 instead of 9)
+#endif
+#ifndef LBM_SHARED_RCP
+#define LBM_SHARED_RCP 0  // FP32: one reciprocal for y_0 and the four opposite-pair products
+#endif
+#ifndef LBM_YFORM
+#define LBM_YFORM 1  // 2-byte storage: start point and result as full populations (see below)
+#endif
+
+// Sign bits of f_a per lane -> ST_UNSTABLE bits (f finite).
+template <typename T, int Q>
+__device__ __forceinline__ uint32_t negative_status(const T (&f)[Q]) {
+    using N = Num<T>;
+    uint32_t st = 0;
+#pragma unroll
+    for (int l = 0; l < N::LANES; ++l) {
+        uint32_t bits = 0u;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) bits |= __float_as_uint(N::lane(f[a], l));
+        st |= (bits >> 31) ? (ST_UNSTABLE << (2 * l)) : 0u;
+    }
+    return st;
+}
+
 // ---------------------------------------------------------------------------
 // D2Q9 MinxEnt collision of one fluid node (or two, T = F2).
 //   NFREE  4 (MinxEnt4: free M2, M3, M5, M7) or 2 (MinxEnt2: free M2, M3)
+//   YFORM  FP32 with 2-byte storage: the start point is formed as
+//          y_a = p^start_a / W_a directly and the result as the full
+//          population f_a, whose deviation f_a - W_a rho0 is taken last.
+//          That subtraction loses the low bits of small deviations (about
+//          2^-24 W_a rho0 absolute), far below the FP16 / BF16 rounding of
+//          the stored deviation, and saves the separate deviation variables.
 //   d      pulled pre-collision deviations f_a - W_a rho0
 //   rho0   reference density; r.omega = 1/tau, r.omega2 = 1/tau2
 //   out    post-collision deviations
@@ -182,11 +214,13 @@ __device__ __forceinline__ void spd4_solve(T a11, T a21, T a22, T a31, T a32, T 
 // (the node keeps p^start, which meets every constraint), ST_UNSTABLE when
 // some post-collision population is negative or not finite.
 // ---------------------------------------------------------------------------
-template <typename T, int NFREE>
+template <typename T, int NFREE, bool YFORM = false>
 __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const Rates<T>& r,
                                                  T (&out)[9]) {
     static_assert(NFREE == 4 || NFREE == 2, "MinxEnt4 or MinxEnt2");
     using N = Num<T>;
+    constexpr bool FP64 = std::is_same<T, double>::value;
+    static_assert(!(YFORM && FP64), "the direct form is for 2-byte storage with FP32 arithmetic");
     const T omega = r.omega;
     constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
@@ -207,7 +241,7 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     const T k = (T(1.0) - omega) * T(0.25);
     const T c8 = (T(9.0) * k) * N::mad(pxx, ir, uyy - uxx);
     const T c9 = (T(36.0) * k) * N::mad(pxy, ir, -(ux * uy));
-    // delta_a = p^start_a / W_a - 1
+    // delta_a = p^start_a / W_a - 1 = (even part s) +- 3 (odd part h)
     const T C1 = T(1.0), C3 = T(3.0), C45 = T(4.5);
     const T b0 = T(-1.5) * (uxx + uyy);
     const T sx = N::mad(C45, uxx, b0 + c8);
@@ -215,7 +249,6 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     const T sp_ = ux + uy, dm_ = uy - ux;
     const T sp = N::mad(C45 * sp_, sp_, b0 + c9);
     const T sm = N::mad(C45 * dm_, dm_, b0 - c9);
-    T del[9];
     // coefficients of the terms odd in v: 3 v.u, plus for MinxEnt2 the
     // relaxed heat flux, T_5a g_x / (12 W_a) = (-3/2 on +x, +3 on (+,+) ...)
     T hx = ux, hy = uy, lp = sp_, lm = dm_;
@@ -231,46 +264,63 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         lp = sp_ + (gx + gy);
         lm = dm_ + (gy - gx);
     }
-    del[0] = b0;
-    del[1] = N::mad(C3, hx, sx);
-    del[3] = N::mad(-C3, hx, sx);
-    del[2] = N::mad(C3, hy, sy);
-    del[4] = N::mad(-C3, hy, sy);
-    del[5] = N::mad(C3, lp, sp);
-    del[7] = N::mad(-C3, lp, sp);
-    del[6] = N::mad(C3, lm, sm);
-    del[8] = N::mad(-C3, lm, sm);
-
-    // y_a = p^start_a / W_a; all positive <=> the logarithms exist (reading C-NEG)
-    T y[9];
+    // y_a = p^start_a / W_a = 1 + delta_a; all positive <=> the logarithms
+    // exist (reading C-NEG).  cx .. cm: the even parts 1 + s of the opposite
+    // pairs (the mean of y_a and y_opp(a)).
+    T del[9], y[9];
+    const T cx = C1 + sx, cy = C1 + sy, cp = C1 + sp, cm = C1 + sm;
+    if constexpr (YFORM) {
+        y[0] = C1 + b0;
+        y[1] = N::mad(C3, hx, cx);
+        y[3] = N::mad(-C3, hx, cx);
+        y[2] = N::mad(C3, hy, cy);
+        y[4] = N::mad(-C3, hy, cy);
+        y[5] = N::mad(C3, lp, cp);
+        y[7] = N::mad(-C3, lp, cp);
+        y[6] = N::mad(C3, lm, cm);
+        y[8] = N::mad(-C3, lm, cm);
+    } else {
+        del[0] = b0;
+        del[1] = N::mad(C3, hx, sx);
+        del[3] = N::mad(-C3, hx, sx);
+        del[2] = N::mad(C3, hy, sy);
+        del[4] = N::mad(-C3, hy, sy);
+        del[5] = N::mad(C3, lp, sp);
+        del[7] = N::mad(-C3, lp, sp);
+        del[6] = N::mad(C3, lm, sm);
+        del[8] = N::mad(-C3, lm, sm);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) y[a] = C1 + del[a];
+        for (int a = 0; a < 9; ++a) y[a] = C1 + del[a];
+    }
     // FP64: the exact test of reading C-NEG.  FP32: see the Newton-step test below.
     typename N::Pred ok{};
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (FP64) {
         const T mn = N::vmin(N::vmin(N::vmin(y[0], y[1]), N::vmin(y[2], y[3])),
                              N::vmin(N::vmin(y[4], y[5]), N::vmin(N::vmin(y[6], y[7]), y[8])));
         ok = N::gt(mn, T(0.0));
     }
 
-    // ln(p/W) (natural or base-2 logs, see Num::LOG_SCALE) and q_a = W_a / p_a
-    T L[9], q[9];
-    // FP32 MinxEnt2 needs only the energy-row gradient (b_e, b_p): it takes
-    // the logarithms of y_0 and of the axis and diagonal products (3 MUFU
-    // operations instead of 9); MinxEnt4 keeps one logarithm per population,
-    // which measured faster there.
-    constexpr bool LOGP = !std::is_same<T, double>::value && NFREE == 2;
-    if constexpr (!LOGP) {
-#pragma unroll
-        for (int a = 0; a < 9; ++a) L[a] = N::lnp(del[a], y[a]);
-    }
-    T p13 = T(0.0), p24 = T(0.0), p57 = T(0.0), p68 = T(0.0);
-    if constexpr (!std::is_same<T, double>::value) {
-        // FP32: opposite populations share one reciprocal of their product
-        // (5 reciprocals instead of 9, each result within ~2 ulp)
+    // q_a = W_a / p_a = 1 / y_a.  FP32: opposite populations share one
+    // reciprocal of their product (each result within ~2 ulp); with
+    // LBM_SHARED_RCP the four products and y_0 share a single one.
+    T q[9];
+    T p13 = T(0.0), p24 = T(0.0), p57 = T(0.0), p68 = T(0.0), pa = T(0.0), pd = T(0.0);
+    if constexpr (!FP64) {
         p13 = y[1] * y[3]; p24 = y[2] * y[4]; p57 = y[5] * y[7]; p68 = y[6] * y[8];
-        const T r13 = N::rcp(p13), r24 = N::rcp(p24), r57 = N::rcp(p57), r68 = N::rcp(p68);
-        q[0] = N::rcp(y[0]);
+        T r13, r24, r57, r68;
+        if constexpr (LBM_SHARED_RCP) {
+            pa = p13 * p24;
+            pd = p57 * p68;
+            const T pad = pa * pd;
+            const T R = N::rcp(y[0] * pad);  // 1 / (y0 pa pd)
+            q[0] = R * pad;
+            const T Rad = R * y[0];          // 1 / (pa pd)
+            const T ra = Rad * pd, rd = Rad * pa;
+            r13 = ra * p24; r24 = ra * p13; r57 = rd * p68; r68 = rd * p57;
+        } else {
+            r13 = N::rcp(p13); r24 = N::rcp(p24); r57 = N::rcp(p57); r68 = N::rcp(p68);
+            q[0] = N::rcp(y[0]);
+        }
         q[1] = y[3] * r13; q[3] = y[1] * r13;
         q[2] = y[4] * r24; q[4] = y[2] * r24;
         q[5] = y[7] * r57; q[7] = y[5] * r57;
@@ -279,6 +329,43 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
 #pragma unroll
         for (int a = 0; a < 9; ++a) q[a] = N::rcp(y[a]);
     }
+
+    // Gradient terms ln(p/W) (natural or base-2 logs, see Num::LOG_SCALE):
+    // L0 of the rest population, La / Ld the sums over the axis / diagonal
+    // populations, D31 = L3 - L1, D42 = L4 - L2, l57 = L5 - L7, l68 = L6 - L8.
+    // FP32 MinxEnt2 needs only L0, La, Ld: logarithms of y_0 and of the axis
+    // and diagonal products (3 instead of 9).  FP32 MinxEnt4 with
+    // LBM_MX4_LOGP takes the differences as logarithms of the quotients
+    // y_a q_opp(a) as well (7 instead of 9).
+    constexpr bool LOGP = !FP64 && (NFREE == 2 || LBM_MX4_LOGP);
+    T L0, La, Ld, D31 = T(0.0), D42 = T(0.0), l57 = T(0.0), l68 = T(0.0);
+    if constexpr (LOGP) {
+        if constexpr (!LBM_SHARED_RCP) {
+            pa = p13 * p24;
+            pd = p57 * p68;
+        }
+        L0 = N::lnp(T(0.0), y[0]);
+        La = N::lnp(T(0.0), pa);
+        Ld = N::lnp(T(0.0), pd);
+        if constexpr (NFREE == 4) {
+            D31 = N::lnp(T(0.0), y[3] * q[1]);
+            D42 = N::lnp(T(0.0), y[4] * q[2]);
+            l57 = N::lnp(T(0.0), y[5] * q[7]);
+            l68 = N::lnp(T(0.0), y[6] * q[8]);
+        }
+    } else {
+        T L[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) L[a] = N::lnp(YFORM ? T(0.0) : del[a], y[a]);
+        L0 = L[0];
+        La = (L[1] + L[2]) + (L[3] + L[4]);
+        Ld = (L[5] + L[6]) + (L[7] + L[8]);
+        D31 = L[3] - L[1];
+        D42 = L[4] - L[2];
+        l57 = L[5] - L[7];
+        l68 = L[6] - L[8];
+    }
+
     // A/9 with 1/p_a = q_a / W_a: rest 9/4 q, axis 9 q, diagonal 36 q.
     const T e13 = q[1] + q[3], e24 = q[2] + q[4];
     const T d13 = q[1] - q[3], d24 = q[2] - q[4];
@@ -287,34 +374,26 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     const T Qa = e13 + e24;
     const T qd = s57 + s68;
     const T dx = d57 - d68, dy = d57 + d68;
-    // rows of T used: e (M2), eps (M3), q_x (M5), q_y (M7)
+    // rows of T used: e (M2), eps (M3), q_x (M5), q_y (M7).  The system is
+    // solved in the scaled unknowns (s~_e, 2 s~_eps, 2 s~_x, 2 s~_y), i.e.
+    // for D A D and D b with D = diag(1, 1/2, 1/2, 1/2): this removes the
+    // common factors 2 and 4 of the eps, q_x and q_y rows of A/9.
     const T A_ee = N::mad(T(16.0), qd, N::mad(T(4.0), q[0], Qa));
-    const T A_ep = N::mad(T(8.0), qd, N::mad(T(-4.0), q[0], Qa + Qa));
-    const T A_pp = T(4.0) * (q[0] + Qa + qd);
-    T L0, La, Ld;
-    if constexpr (LOGP) {
-        L0 = N::lnp(del[0], y[0]);
-        La = N::lnp(T(0.0), p13 * p24);
-        Ld = N::lnp(T(0.0), p57 * p68);
-    } else {
-        L0 = L[0];
-        La = (L[1] + L[2]) + (L[3] + L[4]);
-        Ld = (L[5] + L[6]) + (L[7] + L[8]);
-    }
+    const T A_ep = N::mad(T(4.0), qd, N::mad(T(-2.0), q[0], Qa));
+    const T A_pp = (q[0] + Qa) + qd;
     const T b_e = N::mad(T(-4.0), L0, N::mad(T(2.0), Ld, -La));
-    const T b_p = N::mad(T(4.0), L0, N::mad(T(-2.0), La, Ld));
+    const T b_p = N::mad(T(2.0), L0, N::mad(T(0.5), Ld, -La));
     T se, sps, sx_ = T(0.0), sy_ = T(0.0);
     if constexpr (NFREE == 4) {
-        const T A_ex = N::mad(T(8.0), dx, d13 + d13);
-        const T A_px = T(4.0) * (d13 + dx);
-        const T A_xx = T(4.0) * (e13 + qd);
-        const T A_ey = N::mad(T(8.0), dy, d24 + d24);
-        const T A_py = T(4.0) * (d24 + dy);
-        const T A_yy = T(4.0) * (e24 + qd);
-        const T A_xy = T(4.0) * (s57 - s68);
-        const T l57 = L[5] - L[7], l68 = L[6] - L[8];
-        const T b_x = N::mad(T(2.0), L[3] - L[1], l57 - l68);
-        const T b_y = N::mad(T(2.0), L[4] - L[2], l57 + l68);
+        const T A_ex = N::mad(T(4.0), dx, d13);
+        const T A_px = d13 + dx;
+        const T A_xx = e13 + qd;
+        const T A_ey = N::mad(T(4.0), dy, d24);
+        const T A_py = d24 + dy;
+        const T A_yy = e24 + qd;
+        const T A_xy = s57 - s68;
+        const T b_x = N::mad(T(0.5), l57 - l68, D31);
+        const T b_y = N::mad(T(0.5), l57 + l68, D42);
         spd4_solve<T>(A_ee, A_ep, A_pp, A_ex, A_px, A_xx, A_ey, A_py, A_xy, A_yy, b_e, b_p, b_x,
                       b_y, se, sps, sx_, sy_);
     } else {
@@ -325,7 +404,7 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     }
     // a node whose start point is not positive keeps p^start (reading C-NEG)
     bool rare = false;  // some lane skipped its Newton step (FP32 paths)
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (FP64) {
         se = N::sel(ok, se, T(0.0));
         sps = N::sel(ok, sps, T(0.0));
         if constexpr (NFREE == 4) {
@@ -339,16 +418,21 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         // +0 for finite c and NaN otherwise.
         T chk = (NFREE == 4) ? (se + sps) + (sx_ + sy_) : se + sps;
         chk = chk - chk;
-        // logarithms of products: two negative y can cancel in a product, so
-        // the sign bits of y are tested explicitly
+        // logarithms of products and quotients: two negative y can cancel.
+        // MinxEnt2 tests the sign bits of every y; MinxEnt4 (whose quotients
+        // catch a single negative population of a pair) tests y_0 and the
+        // pair means c, which are negative when both of a pair are.
         uint32_t neg[N::LANES];
 #pragma unroll
         for (int l = 0; l < N::LANES; ++l) {
             neg[l] = 0u;
-            if constexpr (LOGP) {
+            if constexpr (LOGP && NFREE == 2) {
 #pragma unroll
                 for (int a = 0; a < 9; ++a) neg[l] |= __float_as_uint(N::lane(y[a], l));
                 neg[l] >>= 31;
+            } else if constexpr (LOGP) {
+                neg[l] = (__float_as_uint(N::lane(cx, l)) | __float_as_uint(N::lane(cy, l)) |
+                          __float_as_uint(N::lane(cp, l)) | __float_as_uint(N::lane(cm, l))) >> 31;
             }
         }
 #pragma unroll
@@ -367,40 +451,53 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
             }
         }
     }
-    // (T^T s~)_a
+    // (T^T s~)_a from the scaled solution (sps, sx_, sy_ hold twice s~_eps,
+    // s~_x, s~_y)
     T t[9];
-    const T ce = N::mad(T(-2.0), sps, -se);
-    const T cd = N::mad(T(2.0), se, sps);
-    t[0] = T(4.0) * (sps - se);
+    const T ce = -(se + sps);
+    const T cd = N::mad(T(0.5), sps, se + se);
+    t[0] = N::mad(T(-4.0), se, sps + sps);
     if constexpr (NFREE == 4) {
         const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
-        t[1] = N::mad(T(-2.0), sx_, ce);
-        t[3] = N::mad(T(2.0), sx_, ce);
-        t[2] = N::mad(T(-2.0), sy_, ce);
-        t[4] = N::mad(T(2.0), sy_, ce);
-        t[5] = cd + pxy_;
-        t[7] = cd - pxy_;
-        t[6] = cd - mxy_;
-        t[8] = cd + mxy_;
+        t[1] = ce - sx_;
+        t[3] = ce + sx_;
+        t[2] = ce - sy_;
+        t[4] = ce + sy_;
+        t[5] = N::mad(T(0.5), pxy_, cd);
+        t[7] = N::mad(T(-0.5), pxy_, cd);
+        t[6] = N::mad(T(-0.5), mxy_, cd);
+        t[8] = N::mad(T(0.5), mxy_, cd);
     } else {
         t[1] = t[2] = t[3] = t[4] = ce;
         t[5] = t[6] = t[7] = t[8] = cd;
     }
-    // d^post_a = W_a (drho + rho delta_a) - rho (T^T s~)_a; the 1/9 of A's
-    // scaling and the log base go into the last factor.
+    // f^post_a = rho W_a (y_a - (T^T s~)_a); the 1/9 of A's scaling and the
+    // log base go into the last factor.
     const T rs = rho * T(N::LOG_SCALE / 9.0);
+    if constexpr (YFORM) {
+        T f[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const T wa = T(W[a]);
-        out[a] = N::mad(-rs, t[a], N::mad(wa * rho, del[a], wa * drho));
-    }
-    if constexpr (std::is_same<T, double>::value) {
-        return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
-    } else {
+        for (int a = 0; a < 9; ++a) {
+            f[a] = N::mad(-rs, t[a], (T(W[a]) * rho) * y[a]);
+            out[a] = f[a] - T(W[a]) * rho0;
+        }
         if (rare) return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
-        // every step was finite, and so are the populations: only the sign of
-        // f^post = W rho0 + out remains to test (OR of the sign bits)
-        return sign_status<T, 9>(out, W, rho0);
+        return negative_status<T, 9>(f);
+    } else {
+        // d^post_a = W_a (drho + rho delta_a) - rho (T^T s~)_a
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const T wa = T(W[a]);
+            out[a] = N::mad(-rs, t[a], N::mad(wa * rho, del[a], wa * drho));
+        }
+        if constexpr (FP64) {
+            return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
+        } else {
+            if (rare) return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
+            // every step was finite, and so are the populations: only the sign of
+            // f^post = W rho0 + out remains to test (OR of the sign bits)
+            return sign_status<T, 9>(out, W, rho0);
+        }
     }
 }
 
@@ -537,34 +634,39 @@ __device__ __forceinline__ uint32_t bgk_d1q3(const T (&d)[3], T rho0, const Rate
     return lane_status<T>(all, finite_nonneg<T, 3>(out, W, rho0));
 }
 
-// Dispatch by lattice and rule.
-template <class Lat, int COLL, typename T> struct Collide;
-template <typename T> struct Collide<D2Q9, COLL_MINXENT4, T> {
+// Dispatch by lattice, rule, number type and storage bytes SB (the MinxEnt
+// rules take the direct start-point form for 2-byte storage, see
+// minxent_d2q9).  Every kernel passes its own storage size, so all kernels
+// of one context run the same arithmetic.
+template <class Lat, int COLL, typename T, int SB = 8> struct Collide;
+template <typename T, int SB> struct Collide<D2Q9, COLL_MINXENT4, T, SB> {
     __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
                                                    T (&o)[9]) {
-        return minxent_d2q9<T, 4>(d, rho0, r, o);
+        return minxent_d2q9<T, 4, LBM_YFORM && SB == 2 && !std::is_same<T, double>::value>(
+            d, rho0, r, o);
     }
 };
-template <typename T> struct Collide<D2Q9, COLL_MINXENT2, T> {
+template <typename T, int SB> struct Collide<D2Q9, COLL_MINXENT2, T, SB> {
     __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
                                                    T (&o)[9]) {
-        return minxent_d2q9<T, 2>(d, rho0, r, o);
+        return minxent_d2q9<T, 2, LBM_YFORM && SB == 2 && !std::is_same<T, double>::value>(
+            d, rho0, r, o);
     }
 };
-template <typename T> struct Collide<D2Q9, COLL_SRT, T> {
+template <typename T, int SB> struct Collide<D2Q9, COLL_SRT, T, SB> {
     __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
                                                    T (&o)[9]) {
         return srt_d2q9<T>(d, rho0, r, o);
     }
 };
-template <typename T> struct Collide<D2Q9, COLL_MRT, T> {
+template <typename T, int SB> struct Collide<D2Q9, COLL_MRT, T, SB> {
     __device__ static __forceinline__ uint32_t run(const T (&d)[9], T rho0, const Rates<T>& r,
                                                    T (&o)[9]) {
         return mrt_d2q9<T>(d, rho0, r, o);
     }
 };
 // D1Q3: every rule reduces to BGK (one non-conserved moment, relaxed at 1/tau)
-template <int C, typename T> struct Collide<D1Q3, C, T> {
+template <int C, typename T, int SB> struct Collide<D1Q3, C, T, SB> {
     __device__ static __forceinline__ uint32_t run(const T (&d)[3], T rho0, const Rates<T>& r,
                                                    T (&o)[3]) {
         return bgk_d1q3<T>(d, rho0, r, o);

@@ -134,6 +134,8 @@ struct StepArgs {
     const void* tmaps_halo;      // the tile box and with the halo box,
     const void* tmaps_dst;       // and of dst with the tile box (the stores)
     unsigned int* error;         // device error word (bounded waits that ran out)
+    int32_t spin_limit;          // polls of one bounded mbarrier wait (TMA kernel)
+    int32_t lost_tile;           // test hook: tile whose copies are never issued (-1: none)
 };
 
 __host__ __device__ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }

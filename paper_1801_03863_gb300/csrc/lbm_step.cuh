@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs args) {
                     else N::set_lane(d[a], l, to_compute<float, S>(s));
                 }
             }
-            uint32_t st = Collide<Lat, COLL, CT>::run(d, rho0v, rates, o);
+            uint32_t st = Collide<Lat, COLL, CT, (int)sizeof(S)>::run(d, rho0v, rates, o);
             if (cavity_edge) {
 #pragma unroll
                 for (int l = 0; l < P; ++l) {

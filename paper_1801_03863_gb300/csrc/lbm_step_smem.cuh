@@ -57,12 +57,12 @@ namespace lbm {
 #endif
 
 template <typename S, int TILE = (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4),
-          int NST = LBM_SMEM_STAGES>
+          int NST = LBM_SMEM_STAGES, int NTHREADS = 256>
 struct SmemTile {
     static constexpr int E = 16 / (int)sizeof(S);  // elements per 16-byte chunk
     static constexpr int TILE_NODES = TILE;        // X * R
     static constexpr int STAGES = NST;             // depth of the shared-memory ring
-    static constexpr int THREADS = 256;
+    static constexpr int THREADS = NTHREADS;
     static constexpr int WARPS = THREADS / 32;
     // units (32 node pairs = 64 nodes of one row) per warp; a warp's units
     // cover whole rows for X <= 64 * UNITS (smem_tile_width keeps to that)
@@ -70,7 +70,8 @@ struct SmemTile {
     static constexpr int MAX_ROWS = TILE_NODES / 64;  // R at X = 64
     // one plane: the dense R x X tile, then its halo column (one 16-byte
     // chunk per row, room for MAX_ROWS rows)
-    static constexpr int HALO_ELEMS = MAX_ROWS * E;
+    static constexpr int HALO_ELEMS =
+        (MAX_ROWS * E + 128 / (int)sizeof(S) - 1) / (128 / (int)sizeof(S)) * (128 / (int)sizeof(S));
     static constexpr int PLANE_ELEMS = TILE_NODES + HALO_ELEMS;
     static constexpr int PLANE_BYTES = PLANE_ELEMS * (int)sizeof(S);
     static constexpr int HALO_OFF = TILE_NODES * (int)sizeof(S);  // bytes into a plane
@@ -83,6 +84,7 @@ struct SmemTile {
     static constexpr size_t BARS_OFF = PARAMS_OFF + PARAMS_BYTES * STAGES;
     static constexpr size_t SMEM_BYTES = 128 + BARS_OFF + 16 * STAGES;
     static_assert(UNITS >= 1 && UNITS <= 4, "a unit's halo chunk parks at most 3 values");
+    static_assert(TILE_NODES % (2 * THREADS) == 0, "whole units per warp");
     static_assert(HALO_OFF % 128 == 0 && PLANE_BYTES % 128 == 0,
                   "tile blocks and halo columns must stay 128-byte aligned");
 };
@@ -99,8 +101,9 @@ static_assert(sizeof(StageParams) <= 256, "stage parameters must fit 256 bytes")
 static_assert(offsetof(StageParams, in) == 0, "the descriptor copy starts the slot");
 
 // Bounded spin limit of one mbarrier wait (each try_wait may itself suspend
-// for a while); a copy that has not landed by then is treated as lost.
-constexpr int MBAR_SPIN_LIMIT = 1 << 20;
+// for a while): StepArgs::spin_limit polls, 2^20 unless the context was
+// created with a smaller LBM_SPIN_LIMIT (tests of the timeout path); a copy
+// that has not landed by then is treated as lost.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -130,8 +133,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -286,10 +289,10 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
 // results agree bit for bit: the compiler may fuse a packed product into a
 // following packed add, and it does so alike wherever the collision is
 // inlined, which scalar code would not reproduce.
-template <typename S, int COLL, int TILE, int NST>
-__global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
+template <typename S, int COLL, int TILE, int NST, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
     step_kernel_smem(const StepArgs args) {
-    using TS = SmemTile<S, TILE, NST>;
+    using TS = SmemTile<S, TILE, NST, NTHREADS>;
     constexpr int E = TS::E;
     constexpr int Q = 9;
     constexpr int NS = TS::STAGES;
@@ -356,7 +359,8 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     auto release = [&](int j) -> bool {
         const int st = j % NS, fill = j / NS;
         if (fill == 0) return true;
-        if (!mbar_wait_bounded(&empty[st], (uint32_t)((fill - 1) & 1))) return false;
+        if (!mbar_wait_bounded(&empty[st], (uint32_t)((fill - 1) & 1), args.spin_limit))
+            return false;
         store_tile(j - NS);
         nstored = j - NS + 1;
         return true;
@@ -366,6 +370,9 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
         bulk_wait_read();
         const TileDesc tile = next;
         if (j + 1 < ntl) next = args.tiles[blockIdx.x + (j + 1) * G];
+        // test hook of the timeout path: the copies of one chosen tile are
+        // never issued, so its full barrier never completes
+        if ((int)blockIdx.x + j * G == args.lost_tile) return;
         StageParams& p = params[st];
         const int X = tile.pad, R = TS::TILE_NODES / X;
         p.inst = tile.inst; p.X = X; p.x0 = tile.cx0; p.y0 = tile.y0;
@@ -404,7 +411,8 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
         // takes tile j + NS - 1, filled after this thread's first unit
         bool refill = tid == 0 && issued < ntl && issued == j + NS - 1;
         if (refill && !release(issued)) fail = true;
-        if (!fail && !mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1))) fail = true;
+        if (!fail && !mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1), args.spin_limit))
+            fail = true;
         if (fail) break;
         jdone = j;
 
@@ -464,7 +472,7 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
                 CT o[Q];
                 uint32_t sts;
                 if constexpr (INTERIOR) {
-                    sts = Collide<D2Q9, COLL, CT>::run(d, rho0v, rates, o);
+                    sts = Collide<D2Q9, COLL, CT, ES>::run(d, rho0v, rates, o);
                     if (sts) {  // rare: some lane skipped its Newton step or is unstable
                         n_skip += __popc(sts & (ST_NEWTON_SKIPPED * 5u));
                         n_unst += __popc(sts & (ST_UNSTABLE * 5u));
@@ -487,7 +495,7 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
                             d[a] = F2(g);
                         }
                     }
-                    sts = Collide<D2Q9, COLL, CT>::run(d, rho0v, rates, o);
+                    sts = Collide<D2Q9, COLL, CT, ES>::run(d, rho0v, rates, o);
                     if (edge && bc == BC_CAVITY) {
 #pragma unroll
                         for (int l = 0; l < P; ++l) {
@@ -548,7 +556,7 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
     if (tid == 0 && !fail) {
         for (; nstored < ntl; ++nstored) {
             const int j = nstored;
-            if (!mbar_wait_bounded(&empty[j % NS], (uint32_t)((j / NS) & 1))) {
+            if (!mbar_wait_bounded(&empty[j % NS], (uint32_t)((j / NS) & 1), args.spin_limit)) {
                 fail = true;
                 break;
             }
@@ -561,28 +569,30 @@ __global__ void __launch_bounds__(256, LBM_SMEM_MINBLOCKS)
         atomicOr(args.error, 1u);
         if (tid == 0) {
             for (int j = jdone + 1; j < issued; ++j)
-                mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1));
+                mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), args.spin_limit);
         }
     }
     if (tid == 0) bulk_wait_all();  // the stores leave no shared-memory reads behind
 }
 
 // The TMA-staged D2Q9 kernel for a collision rule and tile geometry VARIANT
-// (0: large tiles, 1: small tiles, see smem_tile_nodes); *smem_bytes
-// receives its dynamic shared memory size.
+// (0: large tiles, 1: small tiles, 2: wide CTAs, see smem_tile_nodes);
+// *smem_bytes receives its dynamic shared memory size.
 template <typename S, int VARIANT>
 const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
     constexpr int TN = VARIANT == 0 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4)
-                                    : (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL);
-    constexpr int NS = VARIANT == 0 ? LBM_SMEM_STAGES : LBM_SMEM_STAGES_SMALL;
-    using TS = SmemTile<S, TN, NS>;
+                     : VARIANT == 1 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL)
+                                    : (sizeof(S) == 2 ? LBM_SMEM_TILE2_WIDE : LBM_SMEM_TILE4_WIDE);
+    constexpr int NS = VARIANT == 1 ? LBM_SMEM_STAGES_SMALL : LBM_SMEM_STAGES;
+    constexpr int NT = VARIANT == 2 ? 320 : 256;
+    using TS = SmemTile<S, TN, NS, NT>;
     *smem_bytes = TS::SMEM_BYTES;
     switch (collision) {
-        case COLL_MINXENT4: return (const void*)&step_kernel_smem<S, COLL_MINXENT4, TN, NS>;
-        case COLL_SRT: return (const void*)&step_kernel_smem<S, COLL_SRT, TN, NS>;
-        case COLL_MINXENT2: return (const void*)&step_kernel_smem<S, COLL_MINXENT2, TN, NS>;
+        case COLL_MINXENT4: return (const void*)&step_kernel_smem<S, COLL_MINXENT4, TN, NS, NT>;
+        case COLL_SRT: return (const void*)&step_kernel_smem<S, COLL_SRT, TN, NS, NT>;
+        case COLL_MINXENT2: return (const void*)&step_kernel_smem<S, COLL_MINXENT2, TN, NS, NT>;
         case COLL_MRT:
-        case COLL_TRT: return (const void*)&step_kernel_smem<S, COLL_MRT, TN, NS>;
+        case COLL_TRT: return (const void*)&step_kernel_smem<S, COLL_MRT, TN, NS, NT>;
     }
     return nullptr;
 }

@@ -40,6 +40,8 @@ EXPORTS = (
     "lbm_conservation_noalloc", "lbm_status",
     "lbm_status_instance",
     "lbm_launch_shape", "lbm_destroy", "lbm_status_string",
+    "lbm_init_batch", "lbm_moments_batch", "lbm_moments_batch_device",
+    "lbm_stream_function_batch", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
 )
 
 
@@ -101,6 +103,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lbm_launch_shape": (ctypes.c_int, [P, P]),
             "lbm_destroy": (ctypes.c_int, [P]),
             "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "lbm_init_batch": (ctypes.c_int, [P, I32, P, P, P]),
+            "lbm_moments_batch": (ctypes.c_int, [P, I32, P, P, P]),
+            "lbm_moments_batch_device": (ctypes.c_int, [P, I32, P, P, P]),
+            "lbm_stream_function_batch": (ctypes.c_int, [P, I32, P]),
+            "lbm_state_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64)]),
+            "lbm_save_state": (ctypes.c_int, [P, P]),
+            "lbm_load_state": (ctypes.c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -247,7 +256,56 @@ def lbm_launch_shape(h) -> dict:
     c = np.zeros(5, np.int32)
     _check(load().lbm_launch_shape(h, _p(c)), "lbm_launch_shape")
     return {"V": int(c[0]), "tw": int(c[1]), "th": int(c[2]), "grid": int(c[3]),
-            "kind": {0: "chunks", 1: "smem", 2: "smem_small"}[int(c[4])]}
+            "kind": {0: "chunks", 1: "smem", 2: "smem_small", 3: "smem_wide"}[int(c[4])]}
+
+
+def lbm_init_batch(h, instance: int, rho, ux=None, uy=None) -> None:
+    rho = _f64(rho).reshape(-1)
+    ux = None if ux is None else _f64(ux).reshape(-1)
+    uy = None if uy is None else _f64(uy).reshape(-1)
+    _check(load().lbm_init_batch(h, int(instance), _p(rho), None if ux is None else _p(ux),
+                                 None if uy is None else _p(uy)), "lbm_init_batch")
+
+
+def lbm_moments_batch(h, instance: int, n_nodes: int, want_uy: bool = True,
+                      allow_unstable: bool = False):
+    rho = np.empty(n_nodes)
+    ux = np.empty(n_nodes)
+    uy = np.empty(n_nodes) if want_uy else None
+    code = load().lbm_moments_batch(h, int(instance), _p(rho), _p(ux),
+                                    None if uy is None else _p(uy))
+    _check(code, "lbm_moments_batch", allow_unstable=allow_unstable)
+    return rho, ux, uy, code
+
+
+def lbm_moments_batch_device(h, instance: int, rho_ptr, ux_ptr, uy_ptr) -> None:
+    _check(load().lbm_moments_batch_device(h, int(instance), rho_ptr, ux_ptr, uy_ptr),
+           "lbm_moments_batch_device")
+
+
+def lbm_stream_function_batch(h, instance: int, n_nodes: int,
+                              allow_unstable: bool = False) -> np.ndarray:
+    psi = np.empty(n_nodes)
+    _check(load().lbm_stream_function_batch(h, int(instance), _p(psi)),
+           "lbm_stream_function_batch", allow_unstable=allow_unstable)
+    return psi
+
+
+def lbm_state_bytes(h) -> int:
+    out = ctypes.c_uint64()
+    _check(load().lbm_state_bytes(h, ctypes.byref(out)), "lbm_state_bytes")
+    return int(out.value)
+
+
+def lbm_save_state(h) -> np.ndarray:
+    buf = np.empty(lbm_state_bytes(h), dtype=np.uint8)
+    _check(load().lbm_save_state(h, _p(buf)), "lbm_save_state")
+    return buf
+
+
+def lbm_load_state(h, buf) -> None:
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load().lbm_load_state(h, _p(buf)), "lbm_load_state")
 
 
 def lbm_destroy(h) -> None:
@@ -335,8 +393,29 @@ class Lattice:
         ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
         lbm_init_device(self._h, ptr(rho), ptr(ux), ptr(uy))
 
+    def init_instance(self, i: int, rho, ux=None, uy=None):
+        """Initial equilibrium of instance i alone (before the first step)."""
+        lbm_init_batch(self._h, i, rho, ux, uy)
+
     def step(self, n: int = 1):
         lbm_step(self._h, n)
+
+    def moments_instance(self, i: int, allow_unstable: bool = False):
+        """rho, ux, uy of instance i as [ny, nx] arrays (uy None on D1Q3)."""
+        nx, ny = self.dims[i]
+        r, x, y, _ = lbm_moments_batch(self._h, i, nx * ny, self.q == 9, allow_unstable)
+        return (r.reshape(ny, nx), x.reshape(ny, nx), None if y is None else y.reshape(ny, nx))
+
+    def stream_function_instance(self, i: int, allow_unstable: bool = False) -> np.ndarray:
+        nx, ny = self.dims[i]
+        return lbm_stream_function_batch(self._h, i, nx * ny, allow_unstable).reshape(ny, nx)
+
+    def save_state(self) -> np.ndarray:
+        """Exact checkpoint (raw stored state, step count, counters) as bytes."""
+        return lbm_save_state(self._h)
+
+    def load_state(self, buf):
+        lbm_load_state(self._h, buf)
 
     def moments(self, allow_unstable: bool = False):
         rho, ux, uy, _ = lbm_moments(self._h, self.n_nodes, self.q == 9, allow_unstable)

@@ -6,6 +6,8 @@ GPU's own state (set into the oracle), and (ii) properties that hold at any
 size: conservation, the Taylor-Green decay rate of Eq. (visco-tau), and the
 error of the reduced-precision paths against the FP64 path.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -15,6 +17,8 @@ from paper_1801_03863_gb300 import lbm, workloads as wl
 pytestmark = pytest.mark.gpu
 
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+_VX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
+_VY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
 
 
 def _one_step_vs_oracle(lat, lattice, nx, ny, nu, bc, u_lid=0.0, tol=1e-12, rho0=1.0):
@@ -128,10 +132,24 @@ def test_cavity_2048_config_errors_at_step_1000():
     assert errs["f32"] < errs["f16"] < errs["bf16"], errs
 
 
-def test_cavity_ensemble_64_one_step_and_conservation():
-    """Config: 64 cavities, FP32 compute, FP16 storage.  One step of every
-    node of four instances against the oracle (from the GPU state), and the
-    FP64 conservation totals against the oracle's sums of the same state."""
+def _fp16_one_step_bound(fo, n_nodes):
+    """Per-element bound of one FP32-arithmetic step stored as FP16: the
+    FP16 rounding of each deviation (u = 2^-11, times 1.01 for the FP32
+    arithmetic before it) plus 2e-6 W_a."""
+    dev = np.abs(fo - np.repeat(W9, n_nodes))
+    return 2.0 ** -11 * dev * 1.01 + 2e-6 * np.repeat(W9, n_nodes)
+
+
+@pytest.mark.parametrize("shape", ["smem", "smems"])
+def test_cavity_ensemble_64_one_step_and_conservation(shape, monkeypatch):
+    """Config: 64 cavities, FP32 compute, FP16 storage, on the TMA-staged
+    kernel with large ("smem") and small ("smems") tiles.  One step of every
+    node of seven instances against the oracle (from the GPU state): the four
+    smallest (side 64: every 64-node unit touches a wall), the two largest
+    (1024^2: almost every unit takes the interior fast path) and one whose
+    side is not a multiple of 128 (ragged last tile column); and the FP64
+    conservation totals against the oracle's sums of the same state."""
+    monkeypatch.setenv("LBM_SHAPE", shape)
     members = wl.cavity_ensemble(count=64, seed=0)
     dims = [(m.side, m.side) for m in members]
     rho = np.concatenate([wl.cavity(m.side, noise=1e-6, seed=i)[0].ravel()
@@ -139,6 +157,7 @@ def test_cavity_ensemble_64_one_step_and_conservation():
     z = np.zeros_like(rho)
     with lbm.Lattice("d2q9", dims, [m.nu for m in members], "cavity",
                      u_lid=[m.u_lid for m in members], compute="f32", storage="f16") as lat:
+        assert lat.launch_shape()["kind"] == {"smem": "smem", "smems": "smem_small"}[shape]
         lat.init(rho, z, z)
         lat.step(200)
         f0 = lat.populations()
@@ -146,24 +165,59 @@ def test_cavity_ensemble_64_one_step_and_conservation():
         lat.step(1)
         f1 = lat.populations()
     offs = np.cumsum([0] + [9 * m.side * m.side for m in members])
-    smallest = sorted(range(64), key=lambda i: members[i].side)[:4]
-    for i in smallest:
+    by_side = sorted(range(64), key=lambda i: members[i].side)
+    ragged = [i for i in by_side if members[i].side % 128 != 0 and members[i].side > 128]
+    assert members[by_side[-1]].side == 1024 and ragged
+    for i in by_side[:4] + by_side[-2:] + ragged[-1:]:
         m = members[i]
         n = m.side
         a, b = offs[i], offs[i + 1]
         sim = oracle.Sim(oracle.D2Q9, n, n, oracle.tau_from_nu(m.nu), oracle.BC_CAVITY,
                          u_lid=m.u_lid)
         sim.set_f(f0[a:b])
-        # 2-byte storage: node sums in FP32 (bound 9 * 2^-24 * sum |d|), FP64 across nodes
-        dev0 = f0[a:b] - np.repeat(W9, n * n)
-        np.testing.assert_allclose(cons[i], sim.conservation(), rtol=1e-12,
-                                   atol=9 * 2.0 ** -24 * np.abs(dev0).sum())
+        # the totals against the exactly rounded sums of the same FP64
+        # populations (FP16 deviations are exact in them): the reduction adds
+        # exact node sums in FP64, so only the FP64 rounding of ~n additions
+        # of small partial sums separates the two; the oracle's plain running
+        # sum of 9 n populations is less accurate (~9 n u |total|)
+        fi = f0[a:b].reshape(9, n * n)
+        exact = [math.fsum(fi.ravel()), math.fsum((_VX[:, None] * fi).ravel()),
+                 math.fsum((_VY[:, None] * fi).ravel())]
+        dev_sum = np.abs(fi - W9[:, None]).sum()
+        assert abs(cons[i][0] - exact[0]) <= 1e-14 * exact[0], (cons[i], exact)
+        assert np.abs(cons[i][1:] - exact[1:]).max() <= 1e-12 * dev_sum, (cons[i], exact)
+        np.testing.assert_allclose(cons[i], sim.conservation(), rtol=1e-10,
+                                   atol=1e-10 * dev_sum)
         sim.step(1)
         fo = sim.get_f().ravel()
-        dev_o = fo - np.repeat(W9, n * n)
-        # FP32 arithmetic, then the FP16 rounding of each deviation (u = 2^-11)
-        tol = 2.0 ** -11 * np.abs(dev_o) * 1.01 + 2e-6 * np.repeat(W9, n * n)
-        assert np.all(np.abs(f1[a:b] - fo) <= tol), np.max(np.abs(f1[a:b] - fo) - tol)
+        tol = _fp16_one_step_bound(fo, n * n)
+        assert np.all(np.abs(f1[a:b] - fo) <= tol), (i, n, np.max(np.abs(f1[a:b] - fo) - tol))
+
+
+@pytest.mark.parametrize("shape", ["smem", "smems"])
+def test_cavity_2048_fp16_one_step_vs_oracle(shape, monkeypatch):
+    """Config: cavity 2048^2, U = 0.1, Re = 5000, FP32 compute with FP16
+    storage on the TMA-staged kernel.  After 300 steps, one step of every
+    node (4.2 M nodes, nearly all through the interior fast path) against the
+    oracle's step of the same state (Eq. 2, Sec. IV.E), element by element."""
+    monkeypatch.setenv("LBM_SHAPE", shape)
+    side, u = 2048, 0.1
+    nu = wl.nu_from_reynolds(5000.0, u, side)
+    fields = wl.cavity(side, noise=1e-6, seed=0)
+    with lbm.Lattice("d2q9", [(side, side)], nu, "cavity", u_lid=u, compute="f32",
+                     storage="f16") as lat:
+        lat.init(*fields)
+        lat.step(300)
+        f0 = lat.populations()
+        lat.step(1)
+        f1 = lat.populations()
+        assert lat.status()["unstable"] == 0
+    sim = oracle.Sim(oracle.D2Q9, side, side, oracle.tau_from_nu(nu), oracle.BC_CAVITY, u_lid=u)
+    sim.set_f(f0)
+    sim.step(1)
+    fo = sim.get_f().ravel()
+    tol = _fp16_one_step_bound(fo, side * side)
+    assert np.all(np.abs(f1 - fo) <= tol), np.max(np.abs(f1 - fo) - tol)
 
 
 def test_tube_ensemble_4096_conservation_fp64_totals():
