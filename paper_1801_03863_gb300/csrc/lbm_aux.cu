@@ -252,12 +252,12 @@ __device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, 
 // (P_i = cons_partials(ny_i)); thread t takes x = t, t + CONS_THREADS, ...
 // of each of those rows, rows in increasing order, and the block reduces
 // its threads in a fixed tree into partials[(i*CONS_PARTIALS + b)*3 + c].
-// The order is fixed by the instance alone.  The sums across nodes run in
-// FP64, and so do the node sums of every storage type except FP16, whose
-// node sums are exact integers instead: every FP16 value is a multiple of
-// 2^-24 below 2^16 in magnitude, so 2^24 d is an integer below 2^40 and nine
-// of them add exactly in 64-bit integers (a non-finite value takes the FP64
-// path, so that it propagates).  Interior nodes pull with plain shifted
+// The order is fixed by the instance alone.  The sums run in FP64, except
+// for FP16 storage, where they are exact integers: every FP16 value is a
+// multiple of 2^-24 below 2^16 in magnitude, so 2^24 d is an integer below
+// 2^40, and a thread's nodes add exactly in 64-bit integers, converted to
+// FP64 once (a node with a non-finite value takes the FP64 path, so that it
+// propagates).  Interior nodes pull with plain shifted
 // loads; the outer ring applies the boundary rules.
 template <class Lat, typename S>
 __global__ void __launch_bounds__(CONS_THREADS)
@@ -270,6 +270,7 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
     const int nx = in.nx, ny = in.ny, P = cons_partials(ny);
     const S* base = src + in.off;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    long long i0 = 0, i1 = 0, i2 = 0;  // FP16: exact sums in units of 2^-24
     for (int y = it.y; y < ny; y += P) {
         const bool yint = Lat::Q == 3 || (y >= 1 && y <= ny - 2);
         for (int x = threadIdx.x; x < nx; x += CONS_THREADS) {
@@ -300,10 +301,9 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
                     if (Lat::vy(a) != 0) r2 += Lat::vy(a) > 0 ? v : -v;
                 }
                 if (finite) {
-                    constexpr double inv = 1.0 / 16777216.0;
-                    s0 += (double)r0 * inv;
-                    s1 += (double)r1 * inv;
-                    s2 += (double)r2 * inv;
+                    i0 += r0;
+                    i1 += r1;
+                    i2 += r2;
                     exact = true;
                 }
             }
@@ -317,6 +317,14 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
                 }
             }
         }
+    }
+    if constexpr (std::is_same<S, __half>::value) {
+        // the thread's exact FP16 node sums, in units of 2^-24 (at most
+        // 2^15 nodes of 9 values below 2^40 each: no overflow), to FP64 once
+        constexpr double inv = 1.0 / 16777216.0;
+        s0 += (double)i0 * inv;
+        s1 += (double)i1 * inv;
+        s2 += (double)i2 * inv;
     }
     sh[0][threadIdx.x] = s0;
     sh[1][threadIdx.x] = s1;

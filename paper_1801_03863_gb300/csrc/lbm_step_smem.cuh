@@ -23,20 +23,24 @@
 //    value (deviation 0).
 //  * A ring of STAGES shared-memory stages, each with a "full" mbarrier (the
 //    copies landed) and an "empty" one (every warp is done with it): the
-//    copies of the next tiles are in flight while one is collided.
+//    copies of the next tiles are in flight while one is collided.  No warp
+//    is a dedicated producer: thread 0 fills every stage at the start, and
+//    afterwards the last warp to finish a tile (a per-stage counter tells
+//    which) writes it out and refills the stage with the tile NS later at
+//    once, so a free stage never waits for one particular warp.
 //  * Each warp owns whole rows of the tile and takes them in units of 32
 //    node pairs (one pair per lane, packed FP32x2 arithmetic), left to right.
 //    A unit writes its post-collision pairs back over its own positions in
 //    the stage once every lane has read them; the one value a later unit
 //    still needs from an overwritten position (the pair left of the next
 //    unit's first node) is parked beforehand in the unused words of the
-//    halo chunk.  When every warp is done with a tile, the elected thread
-//    writes the stage's nine planes out with one tensor store each (rows
-//    and chunks beyond the lattice are clipped by the hardware) and waits
-//    for TMA to have read them before the stage is refilled.
+//    halo chunk.  When every warp is done with a tile, the last one writes
+//    the stage's nine planes out with one tensor store each (rows and
+//    chunks beyond the lattice are clipped by the hardware) and waits for
+//    TMA to have read them before it refills the stage.
 //  * Every mbarrier wait is bounded; on timeout the kernel records an error
-//    word and the CTA leaves after a bounded wait for its own copies still
-//    in flight.
+//    word and each warp leaves after a bounded wait for the CTA's copies
+//    still in flight.
 //  * Nodes whose pull crosses a periodic or zero-gradient edge, which a zero
 //    fill cannot express, read their neighbours from global memory with the
 //    boundary rule.
@@ -82,7 +86,10 @@ struct SmemTile {
     static constexpr size_t PARAMS_OFF = STAGES_BYTES;
     static constexpr size_t PARAMS_BYTES = 256;  // per stage
     static constexpr size_t BARS_OFF = PARAMS_OFF + PARAMS_BYTES * STAGES;
-    static constexpr size_t SMEM_BYTES = 128 + BARS_OFF + 16 * STAGES;
+    // two mbarriers per stage, then one warp counter per stage and the
+    // count of tiles whose copies were issued
+    static constexpr size_t COUNT_OFF = BARS_OFF + 16 * STAGES;
+    static constexpr size_t SMEM_BYTES = 128 + COUNT_OFF + 4 * STAGES + 16;
     static_assert(UNITS >= 1 && UNITS <= 4, "a unit's halo chunk parks at most 3 values");
     static_assert(TILE_NODES % (2 * THREADS) == 0, "whole units per warp");
     static_assert(HALO_OFF % 128 == 0 && PLANE_BYTES % 128 == 0,
@@ -95,8 +102,11 @@ struct SmemTile {
 // read both after the wait; the tensor stores read the place).
 struct StageParams {
     InstDesc in;
+    TileDesc next;  // descriptor of the tile this stage takes next (NS tiles later)
     int32_t inst, X, x0, y0;
 };
+static_assert(offsetof(StageParams, next) % 16 == 0 && sizeof(TileDesc) == 16,
+              "the next-tile descriptor is a 16-byte bulk copy");
 static_assert(sizeof(StageParams) <= 256, "stage parameters must fit 256 bytes");
 static_assert(offsetof(StageParams, in) == 0, "the descriptor copy starts the slot");
 
@@ -329,8 +339,15 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
     }
     __syncthreads();
 
-    // Thread 0 writes local tile j out of its stage (every warp is done
-    // with it): one tensor store per plane, then a commit.
+    unsigned int* done = reinterpret_cast<unsigned int*>(smem_al + TS::COUNT_OFF);
+    volatile int* filled = reinterpret_cast<volatile int*>(done + NS);  // tiles filled so far
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k) done[k] = 0u;
+        *filled = 0;
+    }
+
+    // Local tile j out of its stage (every warp is done with it): one
+    // tensor store per plane, then a commit.
     auto store_tile = [&](int j) {
         const StageParams& p = params[j % NS];
         const S* sbase = stage_base + (size_t)(j % NS) * TS::STAGE_ELEMS;
@@ -340,50 +357,31 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
         bulk_commit();
     };
 
-    // Thread 0 refills stage j % NS with local tile j in two parts.  First
-    // (release) it waits until every warp is done with the stage's previous
-    // tile j - NS and hands that tile to the tensor stores; returns false
-    // if the stage was not released in time.  Later (fill) it waits until
-    // TMA has read the stores' sources, stores the tile's place and issues
-    // the descriptor, plane and halo copies on the stage's full barrier.  In
-    // between, thread 0 collides a unit of its own, so the stores are read
-    // out while it computes.  The tile descriptor is fetched one fill ahead,
-    // so no global load waits in thread 0's path.
-    int nstored = 0;  // local tiles handed to TMA stores (thread 0's count)
-    TileDesc next{};  // descriptor of the next tile to fill (thread 0)
-    if (tid == 0 && ntl > 0) next = args.tiles[blockIdx.x];
-    // the tile table and tensor maps are constant; the populations, counters
-    // and error word are read and written only after this
-    wait_previous_grid();
-    allow_next_grid();
-    auto release = [&](int j) -> bool {
-        const int st = j % NS, fill = j / NS;
-        if (fill == 0) return true;
-        if (!mbar_wait_bounded(&empty[st], (uint32_t)((fill - 1) & 1), args.spin_limit))
-            return false;
-        store_tile(j - NS);
-        nstored = j - NS + 1;
-        return true;
-    };
-    auto fill = [&](int j) {
+    // Fill stage j % NS with local tile j (descriptor `tile`): store the
+    // tile's place, then issue the instance-descriptor, plane and halo
+    // copies, and the copy of the descriptor of tile j + NS (which this
+    // stage takes next), all on the stage's full barrier.
+    auto fill = [&](int j, const TileDesc tile) {
         const int st = j % NS;
-        bulk_wait_read();
-        const TileDesc tile = next;
-        if (j + 1 < ntl) next = args.tiles[blockIdx.x + (j + 1) * G];
+        atomicMax((int*)filled, j + 1);
         // test hook of the timeout path: the copies of one chosen tile are
         // never issued, so its full barrier never completes
         if ((int)blockIdx.x + j * G == args.lost_tile) return;
         StageParams& p = params[st];
         const int X = tile.pad, R = TS::TILE_NODES / X;
         p.inst = tile.inst; p.X = X; p.x0 = tile.cx0; p.y0 = tile.y0;
-        const uint32_t bytes =
-            (uint32_t)((Q * R * X + 6 * R * E) * sizeof(S) + sizeof(InstDesc));
+        const bool more = j + NS < ntl;
+        const uint32_t bytes = (uint32_t)((Q * R * X + 6 * R * E) * sizeof(S) + sizeof(InstDesc) +
+                                          (more ? sizeof(TileDesc) : 0));
         S* sbase = stage_base + (size_t)st * TS::STAGE_ELEMS;
         const void* map = &tmaps[tile.inst];
         const void* hmap = &hmaps[tile.inst];
         fence_proxy_async_smem();  // consumers' accesses to this stage come first
         mbar_arrive_expect_tx(&full[st], bytes);
         bulk_load(&p.in, &args.inst[tile.inst], (uint32_t)sizeof(InstDesc), &full[st]);
+        if (more)
+            bulk_load(&p.next, &args.tiles[blockIdx.x + (j + NS) * G], (uint32_t)sizeof(TileDesc),
+                      &full[st]);
 #pragma unroll
         for (int a = 0; a < Q; ++a)
             tma_load_3d(sbase + a * TS::PLANE_ELEMS, map, tile.cx0, tile.y0 - D2Q9::vy(a), a,
@@ -399,22 +397,31 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
         }
     };
 
-    bool fail = false;
-    int issued = 0;  // local tiles handed to TMA loads (thread 0's count)
-    int jdone = -1;  // last local tile whose copies this thread saw land
+    // The tile table and tensor maps are constant; the populations, counters
+    // and error word are read and written only after this.
+    wait_previous_grid();
+    allow_next_grid();
+    __syncthreads();  // counters initialised
+    // thread 0 fills every stage with the CTA's first tiles
     if (tid == 0) {
-        for (; issued < min(NS - 1, ntl); ++issued) fill(issued);
+        for (int j = 0; j < min(NS, ntl); ++j) fill(j, args.tiles[blockIdx.x + j * G]);
     }
-    for (int j = 0; j < ntl && !fail; ++j) {
+
+    // Each warp collides its units of a tile, then its lane 0 arrives on the
+    // stage's empty barrier and counts itself done; the last warp to finish
+    // the tile writes it out and refills the stage with tile j + NS at once
+    // (after TMA has read the stores' sources), so the copies of the next
+    // tiles start as soon as a stage is free, whichever warp frees it.
+    bool fail = false;
+    int j = 0;
+    for (; j < ntl && !fail; ++j) {
         const int st = j % NS;
-        // keep NS - 1 tiles in flight: the stage released by tile j - 1
-        // takes tile j + NS - 1, filled after this thread's first unit
-        bool refill = tid == 0 && issued < ntl && issued == j + NS - 1;
-        if (refill && !release(issued)) fail = true;
-        if (!fail && !mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1), args.spin_limit))
+        // the warp leaves together if the copies did not land in time
+        const bool landed = mbar_wait_bounded(&full[st], (uint32_t)((j / NS) & 1), args.spin_limit);
+        if (!__all_sync(0xffffffffu, landed)) {
             fail = true;
-        if (fail) break;
-        jdone = j;
+            break;
+        }
 
         const StageParams& p = params[st];
         const int X = p.X;
@@ -537,42 +544,47 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
             } else {
                 unit(std::false_type{});
             }
-            if (refill) {
-                fill(issued);
-                ++issued;
-                refill = false;
-            }
         }
-        // this thread's stage writes come before the tensor stores that read them
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
         if (n_skip | n_unst) {
             atomicAdd(args.status + 2 * inst + 0, (unsigned long long)n_skip);
             atomicAdd(args.status + 2 * inst + 1, (unsigned long long)n_unst);
         }
-    }
-    // thread 0 writes out the tiles whose stages were not refilled
-    if (tid == 0 && !fail) {
-        for (; nstored < ntl; ++nstored) {
-            const int j = nstored;
-            if (!mbar_wait_bounded(&empty[j % NS], (uint32_t)((j / NS) & 1), args.spin_limit)) {
-                fail = true;
-                break;
+        // this thread's stage writes come before the tensor stores that read them
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&empty[st]);  // this warp is done with the stage
+            if (atomicAdd(&done[st], 1u) == TS::WARPS - 1) {
+                // last warp of the tile: every other warp has arrived (the
+                // bounded wait gives the acquire), so write the tile out
+                done[st] = 0u;
+                if (!mbar_wait_bounded(&empty[st], (uint32_t)((j / NS) & 1), args.spin_limit)) {
+                    fail = true;
+                } else {
+                    store_tile(j);
+                    if (j + NS < ntl) {
+                        const TileDesc nt = params[st].next;
+                        bulk_wait_read();  // the stores have read the stage
+                        fill(j + NS, nt);
+                    }
+                }
             }
-            store_tile(j);
         }
+        fail = __shfl_sync(0xffffffffu, fail, 0);
     }
     if (fail) {
-        // a copy or a stage release never came: report it and give this
-        // CTA's copies still in flight a bounded chance to land before exit
+        // a copy or a stage release never came: report it and give the
+        // copies still in flight (tiles j .. filled - 1) a bounded chance to
+        // land before this warp leaves
         atomicOr(args.error, 1u);
-        if (tid == 0) {
-            for (int j = jdone + 1; j < issued; ++j)
-                mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), args.spin_limit);
+        if (lane == 0) {
+            const int nf = *filled;
+            for (int t = j; t < nf; ++t)
+                mbar_wait_bounded(&full[t % NS], (uint32_t)((t / NS) & 1), args.spin_limit);
         }
     }
-    if (tid == 0) bulk_wait_all();  // the stores leave no shared-memory reads behind
+    // stores issued by this thread leave no shared-memory reads behind
+    if (lane == 0) bulk_wait_all();
 }
 
 // The TMA-staged D2Q9 kernel for a collision rule and tile geometry VARIANT
