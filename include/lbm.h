@@ -281,15 +281,18 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * with large tiles, 2048 nodes for 2-byte storage or 1024 for FP32, on a
  * two-stage ring, 256 threads; 2: the same kernel with small tiles, 1024 /
  * 512 nodes, on a three-stage ring; 3: wide CTAs of 320 threads with 2560 /
- * 1280-node tiles on a two-stage ring.  For kinds 1 to 3 the tile width is
- * 64/128/256 nodes chosen per instance, at most an eighth of the tile, and
- * out[1], out[2] are 0; tiles go in and out of shared memory by TMA).  Selection: the create-time
+ * 1280-node tiles on a two-stage ring; 4: a deep ring, one CTA of 512
+ * threads per SM with 2048 / 1024-node tiles on four stages.  For kinds 1
+ * to 4 the tile width is 64/128/256 nodes chosen per instance (at most
+ * 32 tile nodes / threads) and out[1], out[2] are 0; tiles go in and out of
+ * shared memory by TMA).  Selection: the create-time
  * autotuner (median of three timed launches per candidate shape; the choice
  * is cached per device, lattice, types, rule, boundary and instance sizes
  * for the life of the process, and in the text file named by the
  * environment variable LBM_AUTOTUNE_CACHE when set, which later processes
  * reuse without timing), or the environment variable LBM_SHAPE = "V,tw,th"
- * (register chunks), "smem" (kind 1), "smems" (kind 2) or "smemw" (kind 3). */
+ * (register chunks), "smem" (kind 1), "smems" (kind 2), "smemw" (kind 3) or
+ * "smemd" (kind 4). */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* out);
 
 /* Destroy a context (NULL-safe).  Frees library-owned memory only. */

@@ -29,9 +29,9 @@ constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even)
 size_t dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
 
 // Launch shape.  kind 0: register-chunk kernel (V nodes per thread, tiles of
-// tw x th chunks); kind 1 / 2 / 3: TMA-staged D2Q9 kernel with node pairs
-// (V = 2) in the large-tile / small-tile / wide-CTA geometry
-// (smem_tile_nodes variant kind - 1), tile width per instance.
+// tw x th chunks); kind 1 / 2 / 3 / 4: TMA-staged D2Q9 kernel with node
+// pairs (V = 2) in the large-tile / small-tile / wide-CTA / deep-ring
+// geometry (smem_tile_nodes variant kind - 1), tile width per instance.
 struct Shape {
     int V, tw, th;
     int kind = 0;
@@ -55,6 +55,7 @@ std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, in
         out.push_back({2, 0, 0, 1});  // TMA-staged kernel, node pairs, large tiles
         out.push_back({2, 0, 0, 2});  // TMA-staged kernel, node pairs, small tiles
         out.push_back({2, 0, 0, 3});  // TMA-staged kernel, node pairs, wide CTAs
+        out.push_back({2, 0, 0, 4});  // TMA-staged kernel, node pairs, deep ring
         out.push_back(default_shape(lattice, storage));
         return out;
     }
@@ -86,7 +87,7 @@ int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const 
     if (s.kind >= 1) {
         for (auto& d : dims) {
             const int tn = smem_tile_nodes(storage, s.kind - 1);
-            const int64_t X = smem_tile_width(d.first, tn);
+            const int64_t X = smem_tile_width(d.first, tn, smem_threads(s.kind - 1));
             const int64_t R = tn / X;
             n += ((d.first + X - 1) / X) * ((d.second + R - 1) / R);
         }
@@ -139,7 +140,8 @@ Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t
     }
     L.max_tiles = std::max({bound, count_tiles(dims, Shape{2, 0, 0, 1}, storage),
                             count_tiles(dims, Shape{2, 0, 0, 2}, storage),
-                            count_tiles(dims, Shape{2, 0, 0, 3}, storage)});
+                            count_tiles(dims, Shape{2, 0, 0, 3}, storage),
+                            count_tiles(dims, Shape{2, 0, 0, 4}, storage)});
     return L;
 }
 
@@ -262,7 +264,7 @@ std::vector<TileDesc> build_tiles(const lbm_ctx* ctx, const Shape& s) {
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
             const int tn = smem_tile_nodes(ctx->storage, s.kind - 1);
-            const int X = smem_tile_width(in.nx, tn);
+            const int X = smem_tile_width(in.nx, tn, smem_threads(s.kind - 1));
             const int R = tn / X;
             for (int64_t y0 = 0; y0 < in.ny; y0 += R)
                 for (int64_t x0 = 0; x0 < in.nx; x0 += X)
@@ -293,7 +295,7 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     const void* k = nullptr;
     size_t smem = 0;
     if (s.kind >= 1) {
-        if (ctx->lattice != 2 || ctx->compute != DT_F32 || s.kind > 3) return LBM_ERR_ARG;
+        if (ctx->lattice != 2 || ctx->compute != DT_F32 || s.kind > 4) return LBM_ERR_ARG;
         const int var = s.kind - 1;
         if (ctx->storage == DT_F32) k = step_kernel_smem_f32(ctx->collision, var, &smem);
         else if (ctx->storage == DT_F16) k = step_kernel_smem_f16(ctx->collision, var, &smem);
@@ -365,7 +367,8 @@ int build_tensor_maps(lbm_ctx* ctx, int variant) {
         const bool halo = (m & 1) != 0;
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
-            const int X = smem_tile_width(in.nx, tile_nodes), R = tile_nodes / X;
+            const int X = smem_tile_width(in.nx, tile_nodes, smem_threads(variant));
+            const int R = tile_nodes / X;
             void* base = ctx->buf[b] + (size_t)in.off * es;
             cuuint64_t dims[3] = {(cuuint64_t)in.nx, (cuuint64_t)in.ny, 9};
             cuuint64_t strides[2] = {(cuuint64_t)in.pitch * es, (cuuint64_t)in.plane * es};
@@ -605,6 +608,11 @@ bool parse_shape_env(Shape* s) {
         *s = {2, 0, 0, 3};
         return true;
     }
+    if (strcmp(e, "smemd") == 0) {
+        *s = {2, 0, 0, 4};
+        return true;
+    }
+
     int v, tw, th;
     if (sscanf(e, "%d,%d,%d", &v, &tw, &th) != 3) return false;
     *s = {v, tw, th};

@@ -89,19 +89,25 @@ const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes
 //      copies in flight, for bandwidth-bound rules);
 //   2  wide CTAs: 2560 / 1280 nodes, 320 threads (ten warps), two-stage
 //      ring: two CTAs give 20 warps per SM instead of 16, at a register
-//      budget of 102 per thread.
+//      budget of 102 per thread;
+//   3  deep ring: one CTA per SM of 512 threads (16 warps) with 2048 /
+//      1024-node tiles on a four-stage ring, so a stage is refilled three
+//      tiles before it is needed.
+#ifndef LBM_SMEM_STAGES_DEEP
+#define LBM_SMEM_STAGES_DEEP 4
+#endif
 inline int smem_tile_nodes(int storage, int variant) {
     if (variant == 1) return storage == 1 ? LBM_SMEM_TILE4_SMALL : LBM_SMEM_TILE2_SMALL;
     if (variant == 2) return storage == 1 ? LBM_SMEM_TILE4_WIDE : LBM_SMEM_TILE2_WIDE;
     return storage == 1 ? LBM_SMEM_TILE4 : LBM_SMEM_TILE2;
 }
-inline int smem_threads(int variant) { return variant == 2 ? 320 : 256; }
+inline int smem_threads(int variant) { return variant == 2 ? 320 : (variant == 3 ? 512 : 256); }
 // Tile width: 64, 128 or 256 nodes by the instance width, at most
-// tile_nodes / 8, so that each warp's units (tile_nodes / (2 * threads)
-// units of 64 nodes) cover whole tile rows.
-inline int smem_tile_width(int64_t nx, int tile_nodes) {
+// 32 tile_nodes / threads, so that each warp's units (tile_nodes /
+// (2 threads) units of 64 nodes) cover whole tile rows.
+inline int smem_tile_width(int64_t nx, int tile_nodes, int threads) {
     int w = nx >= 256 ? 256 : (nx >= 128 ? 128 : 64);
-    while (w > 64 && w > tile_nodes / 8) w /= 2;
+    while (w > 64 && (int64_t)w * threads > 32LL * tile_nodes) w /= 2;
     return w;
 }
 

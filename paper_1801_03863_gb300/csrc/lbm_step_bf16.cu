@@ -13,6 +13,7 @@ const void* step_kernel_bf16(int lattice, int collision, int V) {
 
 const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes) {
     if (variant == 2) return pick_step_kernel_smem<__nv_bfloat16, 2>(collision, smem_bytes);
+    if (variant == 3) return pick_step_kernel_smem<__nv_bfloat16, 3>(collision, smem_bytes);
     return variant == 1 ? pick_step_kernel_smem<__nv_bfloat16, 1>(collision, smem_bytes)
                         : pick_step_kernel_smem<__nv_bfloat16, 0>(collision, smem_bytes);
 }

@@ -13,6 +13,7 @@ const void* step_kernel_f16(int lattice, int collision, int V) {
 
 const void* step_kernel_smem_f16(int collision, int variant, size_t* smem_bytes) {
     if (variant == 2) return pick_step_kernel_smem<__half, 2>(collision, smem_bytes);
+    if (variant == 3) return pick_step_kernel_smem<__half, 3>(collision, smem_bytes);
     return variant == 1 ? pick_step_kernel_smem<__half, 1>(collision, smem_bytes)
                         : pick_step_kernel_smem<__half, 0>(collision, smem_bytes);
 }

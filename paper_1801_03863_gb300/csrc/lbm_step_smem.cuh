@@ -198,6 +198,15 @@ struct UnitOffs {
     uint32_t own, lft, rgt;
 };
 
+// One unit's place: offsets, its row's halo chunk, index within the row,
+// first node (x, y), and whether all its 64 nodes are interior nodes.
+struct UnitGeom {
+    UnitOffs uo;
+    uint32_t hrow;
+    int sg, x, y;
+    bool interior;
+};
+
 // Pair of nodes (2p, 2p+1) of plane `pl` pulled with shift -VX in x, as
 // FP32x2.
 template <typename S, int VX>
@@ -300,7 +309,7 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
 // following packed add, and it does so alike wherever the collision is
 // inlined, which scalar code would not reproduce.
 template <typename S, int COLL, int TILE, int NST, int NTHREADS>
-__global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
+__global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBLOCKS)
     step_kernel_smem(const StepArgs args) {
     using TS = SmemTile<S, TILE, NST, NTHREADS>;
     constexpr int E = TS::E;
@@ -435,30 +444,32 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
         uint32_t n_skip = 0, n_unst = 0;
         const float* lid = p.in.lid_dev_f;  // read where a lid node needs it
         const int inst = p.inst;
-        // one unit at a time (unrolling raises register pressure and measured slower)
-#pragma unroll 1
-        for (int k = 0; k < TS::UNITS; ++k) {
+        // geometry of unit k of this warp
+        auto geom = [&](int k) {
+            UnitGeom g;
             const int u = warp * TS::UNITS + k;
-            const int r = u >> sl2;          // tile row
-            const int sg = u & smask;        // unit within the row
-            const int px = (sg << 5) + lane; // pair within the row
-            const int x = x0 + P * px;
-            const int y = y0 + r;
-            const uint32_t hrow = (uint32_t)(TS::HALO_OFF + r * 16);  // this row's halo chunk
-            UnitOffs uo;
-            uo.own = (uint32_t)((r * X + P * px) * ES);
-            uo.lft = (lane == 0) ? hrow + 4u * (uint32_t)(3 - sg) : uo.own - 4u;
-            uo.rgt = (lane == 31 && sg == smask) ? hrow : uo.own + (uint32_t)(P * ES);
+            const int r = u >> sl2;       // tile row
+            g.sg = u & smask;             // unit within the row
+            const int px = (g.sg << 5) + lane;  // pair within the row
+            g.x = x0 + P * px;
+            g.y = y0 + r;
+            g.hrow = (uint32_t)(TS::HALO_OFF + r * 16);  // this row's halo chunk
+            g.uo.own = (uint32_t)((r * X + P * px) * ES);
+            g.uo.lft = (lane == 0) ? g.hrow + 4u * (uint32_t)(3 - g.sg) : g.uo.own - 4u;
+            g.uo.rgt = (lane == 31 && g.sg == smask) ? g.hrow : g.uo.own + (uint32_t)(P * ES);
             // all 64 nodes of the unit are interior nodes of the lattice (the
-            // same for every lane): no boundary rule, no padding lane.  A
-            // second copy of the unit without the edge logic pays for the
-            // arithmetic-heavy MinxEnt rules only (measured: +2 % MinxEnt4,
-            // -2 % SRT).
-            constexpr bool FAST = COLL == COLL_MINXENT4 || COLL == COLL_MINXENT2;
-            const int xs = x0 + (sg << 6);
-            const bool interior =
-                FAST && (y >= 1) & (y <= ny - 2) & (xs >= 1) & (xs + 63 <= nx - 2);
-            auto unit = [&](auto interior_tag) {
+            // same for every lane): no boundary rule, no padding lane
+            const int xs = x0 + (g.sg << 6);
+            g.interior = (g.y >= 1) & (g.y <= ny - 2) & (xs >= 1) & (xs + 63 <= nx - 2);
+            return g;
+        };
+        // A second copy of the unit without the edge logic pays for the
+        // arithmetic-heavy MinxEnt rules only (measured: +2 % MinxEnt4, -2 % SRT).
+        constexpr bool FAST = COLL == COLL_MINXENT4 || COLL == COLL_MINXENT2;
+            auto unit = [&](auto interior_tag, const UnitGeom& g) {
+                const UnitOffs& uo = g.uo;
+                const uint32_t hrow = g.hrow;
+                const int sg = g.sg, x = g.x, y = g.y;
                 constexpr bool INTERIOR = decltype(interior_tag)::value;
                 CT d[Q];
                 load_unit<S, PB>(sb, uo, d);
@@ -538,13 +549,18 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
                 for (int a = 0; a < Q; ++a)
                     smem_store_pair<S>(sb + a * PB + uo.own, o[a].v.x, o[a].v.y);
             };
+#pragma unroll 1
+        auto single = [&](const UnitGeom& g) {
             if constexpr (FAST) {
-                if (interior) unit(std::true_type{});
-                else unit(std::false_type{});
+                if (g.interior) unit(std::true_type{}, g);
+                else unit(std::false_type{}, g);
             } else {
-                unit(std::false_type{});
+                unit(std::false_type{}, g);
             }
-        }
+        };
+        // one unit at a time (unrolling, or two units collided together,
+        // measured slower: registers)
+        for (int k = 0; k < TS::UNITS; ++k) single(geom(k));
         if (n_skip | n_unst) {
             atomicAdd(args.status + 2 * inst + 0, (unsigned long long)n_skip);
             atomicAdd(args.status + 2 * inst + 1, (unsigned long long)n_unst);
@@ -588,15 +604,17 @@ __global__ void __launch_bounds__(NTHREADS, LBM_SMEM_MINBLOCKS)
 }
 
 // The TMA-staged D2Q9 kernel for a collision rule and tile geometry VARIANT
-// (0: large tiles, 1: small tiles, 2: wide CTAs, see smem_tile_nodes);
+// (0: large tiles, 1: small tiles, 2: wide CTAs, 3: deep ring, see
+// smem_tile_nodes);
 // *smem_bytes receives its dynamic shared memory size.
 template <typename S, int VARIANT>
 const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
-    constexpr int TN = VARIANT == 0 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4)
-                     : VARIANT == 1 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL)
-                                    : (sizeof(S) == 2 ? LBM_SMEM_TILE2_WIDE : LBM_SMEM_TILE4_WIDE);
-    constexpr int NS = VARIANT == 1 ? LBM_SMEM_STAGES_SMALL : LBM_SMEM_STAGES;
-    constexpr int NT = VARIANT == 2 ? 320 : 256;
+    constexpr int TN = VARIANT == 1 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL)
+                     : VARIANT == 2 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2_WIDE : LBM_SMEM_TILE4_WIDE)
+                                    : (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4);
+    constexpr int NS = VARIANT == 1 ? LBM_SMEM_STAGES_SMALL
+                     : VARIANT == 3 ? LBM_SMEM_STAGES_DEEP : LBM_SMEM_STAGES;
+    constexpr int NT = VARIANT == 2 ? 320 : (VARIANT == 3 ? 512 : 256);
     using TS = SmemTile<S, TN, NS, NT>;
     *smem_bytes = TS::SMEM_BYTES;
     switch (collision) {

@@ -256,7 +256,8 @@ def lbm_launch_shape(h) -> dict:
     c = np.zeros(5, np.int32)
     _check(load().lbm_launch_shape(h, _p(c)), "lbm_launch_shape")
     return {"V": int(c[0]), "tw": int(c[1]), "th": int(c[2]), "grid": int(c[3]),
-            "kind": {0: "chunks", 1: "smem", 2: "smem_small", 3: "smem_wide"}[int(c[4])]}
+            "kind": {0: "chunks", 1: "smem", 2: "smem_small", 3: "smem_wide",
+                     4: "smem_deep"}[int(c[4])]}
 
 
 def lbm_init_batch(h, instance: int, rho, ux=None, uy=None) -> None:

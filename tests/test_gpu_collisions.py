@@ -199,14 +199,14 @@ def test_launch_shapes_agree_bitwise(rule, storage, bc, dims, monkeypatch):
     f0 = np.concatenate(parts)
     chunk = "2,16,8" if storage == "f32" else "4,8,16"
     out = {}
-    for s in (chunk, "smem", "smems", "smemw"):
+    for s in (chunk, "smem", "smems", "smemw", "smemd"):
         monkeypatch.setenv("LBM_SHAPE", s)
         with lbm.Lattice("d2q9", dims, nus, bc, u_lid=0.07, compute="f32", storage=storage,
                          collision=rule) as lat:
             lat.set_populations(f0)
             lat.step(21)
             out[s] = (lat.populations(), lat.status())
-    for s in ("smem", "smems", "smemw"):
+    for s in ("smem", "smems", "smemw", "smemd"):
         assert out[s][1] == out[chunk][1], s
         assert np.array_equal(out[s][0], out[chunk][0]), s
 

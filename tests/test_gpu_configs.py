@@ -140,7 +140,7 @@ def _fp16_one_step_bound(fo, n_nodes):
     return 2.0 ** -11 * dev * 1.01 + 2e-6 * np.repeat(W9, n_nodes)
 
 
-@pytest.mark.parametrize("shape", ["smem", "smems", "smemw"])
+@pytest.mark.parametrize("shape", ["smem", "smems", "smemw", "smemd"])
 def test_cavity_ensemble_64_one_step_and_conservation(shape, monkeypatch):
     """Config: 64 cavities, FP32 compute, FP16 storage, on the TMA-staged
     kernel with large ("smem") and small ("smems") tiles and wide CTAs
@@ -159,7 +159,7 @@ def test_cavity_ensemble_64_one_step_and_conservation(shape, monkeypatch):
     with lbm.Lattice("d2q9", dims, [m.nu for m in members], "cavity",
                      u_lid=[m.u_lid for m in members], compute="f32", storage="f16") as lat:
         assert lat.launch_shape()["kind"] == {"smem": "smem", "smems": "smem_small",
-                                              "smemw": "smem_wide"}[shape]
+                                              "smemw": "smem_wide", "smemd": "smem_deep"}[shape]
         lat.init(rho, z, z)
         lat.step(200)
         f0 = lat.populations()
@@ -196,7 +196,7 @@ def test_cavity_ensemble_64_one_step_and_conservation(shape, monkeypatch):
         assert np.all(np.abs(f1[a:b] - fo) <= tol), (i, n, np.max(np.abs(f1[a:b] - fo) - tol))
 
 
-@pytest.mark.parametrize("shape", ["smem", "smems", "smemw"])
+@pytest.mark.parametrize("shape", ["smem", "smems", "smemw", "smemd"])
 def test_cavity_2048_fp16_one_step_vs_oracle(shape, monkeypatch):
     """Config: cavity 2048^2, U = 0.1, Re = 5000, FP32 compute with FP16
     storage on the TMA-staged kernel.  After 300 steps, one step of every

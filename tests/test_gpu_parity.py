@@ -326,7 +326,7 @@ def test_launch_shapes_agree_bitwise(storage, monkeypatch):
     fields = wl.taylor_green(nx, u0=0.05, ny=ny)
     compute = "f64" if storage == "f64" else "f32"
     shapes = ["2,4,32", "2,16,8", "2,64,4"] if storage == "f64" else \
-        ["4,8,16", "8,4,32", "8,32,8", "smem", "smems", "smemw"]
+        ["4,8,16", "8,4,32", "8,32,8", "smem", "smems", "smemw", "smemd"]
     ref = None
     for s in shapes:
         monkeypatch.setenv("LBM_SHAPE", s)
@@ -334,7 +334,8 @@ def test_launch_shapes_agree_bitwise(storage, monkeypatch):
                          storage=storage) as lat:
             sh = lat.launch_shape()
             if s.startswith("smem"):
-                assert sh["kind"] == {"smem": "smem", "smems": "smem_small", "smemw": "smem_wide"}[s]
+                assert sh["kind"] == {"smem": "smem", "smems": "smem_small", "smemw": "smem_wide",
+                                     "smemd": "smem_deep"}[s]
                 assert sh["V"] == 2
             else:
                 assert sh["V"] == int(s.split(",")[0]) and sh["kind"] == "chunks"
@@ -365,13 +366,13 @@ def test_smem_kernel_matches_chunk_kernel(storage, bc, dims, monkeypatch):
         k += nx * ny
     f0 = np.concatenate(parts)
     out = {}
-    for s in ("4,8,16", "smem", "smems", "smemw"):
+    for s in ("4,8,16", "smem", "smems", "smemw", "smemd"):
         monkeypatch.setenv("LBM_SHAPE", s if storage != "f32" or s.startswith("smem") else "2,16,8")
         with lbm.Lattice("d2q9", dims, nus, bc, u_lid=0.07, compute="f32", storage=storage) as lat:
             lat.set_populations(f0)
             lat.step(21)
             out[s] = (lat.populations(), lat.status())
-    for s in ("smem", "smems", "smemw"):
+    for s in ("smem", "smems", "smemw", "smemd"):
         assert out[s][1] == out["4,8,16"][1], s
         assert np.array_equal(out[s][0], out["4,8,16"][0]), s
 
@@ -456,7 +457,7 @@ def test_reduced_precision_taylor_green(storage):
     assert np.abs(r - ro).max() <= bound_r, np.abs(r - ro).max()
 
 
-@pytest.mark.parametrize("shape", ["auto", "smem", "smems", "smemw"])
+@pytest.mark.parametrize("shape", ["auto", "smem", "smems", "smemw", "smemd"])
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_reduced_precision_one_step_every_node(storage, shape, monkeypatch):
     """One step from an FP16-representable state: the only differences are

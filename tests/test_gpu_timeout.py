@@ -22,7 +22,8 @@ def _cavity(nx, ny):
     return np.full(nx * ny, 1.0), np.zeros(nx * ny), np.zeros(nx * ny)
 
 
-@pytest.mark.parametrize("shape,lost", [("smem", 5), ("smem", 0), ("smems", 3), ("smemw", 4)])
+@pytest.mark.parametrize("shape,lost", [("smem", 5), ("smem", 0), ("smems", 3), ("smemw", 4),
+                                               ("smemd", 6)])
 def test_lost_copy_times_out_and_is_reported(shape, lost, monkeypatch):
     nx, ny = 256, 64  # 8 large tiles, 16 small ones, 7 of the wide CTAs' 2560 nodes
     monkeypatch.setenv("LBM_SHAPE", shape)
