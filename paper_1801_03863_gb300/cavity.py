@@ -132,3 +132,37 @@ def ldas_cavity(side: int = LDAS_SIDE, re: float = 1000.0, u_lid: float = 0.01,
             prev = cur
         r, x, y = lat.moments()
     return psi_hat, r.reshape(side, side), x.reshape(side, side), y.reshape(side, side), steps
+
+
+def ldas_batch(u_lids, side: int = LDAS_SIDE, re: float = 1000.0, collision: str = "minxent4",
+               compute: str = "f64", storage: str | None = None, tol: float = 1e-5,
+               check_every: int = 20_000, max_steps: int = 3_000_000, rho0: float = LDAS_RHO):
+    """Several LDAS cavities (one per lid speed, same side and Re) advanced
+    together in one batched context, each checked with its own stream
+    function (``lbm_stream_function_batch``: one member read back, not the
+    whole ensemble) until every member meets Table II's stopping rule.
+    Returns a list of (psi_hat, steps at which the member converged)."""
+    u_lids = [float(u) for u in u_lids]
+    n = len(u_lids)
+    nus = [wl.nu_from_reynolds(re, u, side) for u in u_lids]
+    rho = np.full(side * side * n, rho0)
+    z = np.zeros_like(rho)
+    prev = [None] * n
+    done = [None] * n
+    psi = [None] * n
+    with lbm.Lattice("d2q9", [(side, side)] * n, nus, "cavity", u_lid=u_lids, compute=compute,
+                     storage=storage, collision=collision, rho0=rho0) as lat:
+        lat.init(rho, z, z)
+        steps = 0
+        while steps < max_steps and any(d is None for d in done):
+            lat.step(check_every)
+            steps += check_every
+            for i, u in enumerate(u_lids):
+                if done[i] is not None:
+                    continue
+                psi[i] = normalised_stream_function(lat.stream_function_instance(i), u)
+                cur = float(psi[i].min())
+                if prev[i] is not None and abs(cur - prev[i]) < tol:
+                    done[i] = steps
+                prev[i] = cur
+    return [(psi[i], done[i] if done[i] is not None else steps) for i in range(n)]

@@ -150,34 +150,11 @@ __device__ __forceinline__ uint32_t plain_status(const T (&out)[Q], const double
 // A = L D L^T with unit lower-triangular L, then L z = b, x = L^-T D^-1 z.
 // Four reciprocals (of the pivots) and 32 multiply-adds; A is given as its
 // 10 unique entries, unknown order (1, 2, 3, 4).
-#ifndef LBM_SPD_BLOCK
-#define LBM_SPD_BLOCK 0
-#endif
 template <typename T>
 __device__ __forceinline__ void spd4_solve(T a11, T a21, T a22, T a31, T a32, T a33, T a41, T a42,
                                            T a43, T a44, T b1, T b2, T b3, T b4, T& x1, T& x2,
                                            T& x3, T& x4) {
     using N = Num<T>;
-#if LBM_SPD_BLOCK
-    // 2x2 blocks: P = (1,2), Q = (3,4), C = coupling; Schur complement
-    // S = P - C Q^-1 C^T; two reciprocals on a shorter dependency chain
-    const T rq = N::rcp(N::mad(a33, a44, -(a43 * a43)));
-    const T m11 = N::mad(a31, a44, -(a41 * a43)) * rq, m12 = N::mad(a41, a33, -(a31 * a43)) * rq;
-    const T m21 = N::mad(a32, a44, -(a42 * a43)) * rq, m22 = N::mad(a42, a33, -(a32 * a43)) * rq;
-    const T s11 = a11 - N::mad(m11, a31, m12 * a41);
-    const T s21 = a21 - N::mad(m21, a31, m22 * a41);
-    const T s22 = a22 - N::mad(m21, a32, m22 * a42);
-    const T c1 = b1 - N::mad(m11, b3, m12 * b4);
-    const T c2 = b2 - N::mad(m21, b3, m22 * b4);
-    const T rs = N::rcp(N::mad(s11, s22, -(s21 * s21)));
-    x1 = N::mad(s22, c1, -(s21 * c2)) * rs;
-    x2 = N::mad(s11, c2, -(s21 * c1)) * rs;
-    const T g3 = b3 - N::mad(a31, x1, a32 * x2);
-    const T g4 = b4 - N::mad(a41, x1, a42 * x2);
-    x3 = N::mad(a44, g3, -(a43 * g4)) * rq;
-    x4 = N::mad(a33, g4, -(a43 * g3)) * rq;
-    return;
-#endif
     const T r1 = N::rcp(a11);
     const T l21 = a21 * r1, l31 = a31 * r1, l41 = a41 * r1;
     const T r2 = N::rcp(N::mad(-l21, a21, a22));

@@ -133,3 +133,18 @@ def test_ldss_minxent4_most_stable_near_zero_viscosity():
         assert best["srt"][-1] < best["minxent4"][-1]
         if reading == "magic":
             assert best["srt"][-1] <= min(best[c][-1] for c in ("minxent2", "mrt", "trt"))
+
+
+def test_ldas_batch_members_equal_single_runs():
+    """Members of a batched LDAS context, each read back alone through
+    lbm_stream_function_batch, equal the single-cavity runs bit for bit
+    (the step treats every instance independently); each stops at its own
+    convergence check."""
+    side, re = 33, 100.0
+    res = cavity.ldas_batch([0.05, 0.1], side=side, re=re, tol=1e-4, check_every=500,
+                            max_steps=20_000)
+    for (psi_b, steps_b), u in zip(res, [0.05, 0.1]):
+        psi_s, _, _, _, steps_s = cavity.ldas_cavity(side=side, re=re, u_lid=u, tol=1e-4,
+                                                     check_every=500, max_steps=20_000)
+        assert steps_b == steps_s
+        assert np.array_equal(psi_b, psi_s)
