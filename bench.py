@@ -483,7 +483,9 @@ def run_ours(args, dist):
 
 def e2e_leg(args, lat, wk):
     """Same K steps through the public C ABI with host buffers: upload of the
-    initial fields from pinned memory, the step loop, read-back of rho and u."""
+    initial fields from pinned memory, the step loop with the conservation
+    totals read to the host every CONS_EVERY steps (as in the device-timed
+    loop), read-back of rho and u."""
     import torch
 
     from paper_1801_03863_gb300 import lbm
@@ -492,18 +494,26 @@ def e2e_leg(args, lat, wk):
     pin = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2 * nf)]
     for j, a in enumerate(wk.fields()):
         pin[j].numpy()[:] = a
+    count = len(wk.dims)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lbm.lbm_init(lat._h, *[pin[j].numpy() for j in range(nf)])
-    lbm.lbm_step(lat._h, args.steps)
+    k, chunks = args.steps, 0
+    while k > 0:
+        c = min(CONS_EVERY, k)
+        lbm.lbm_step(lat._h, c)
+        lbm.lbm_conservation(lat._h, count)
+        k -= c
+        chunks += 1
     code = lbm.load().lbm_moments(lat._h, pin[nf].data_ptr(), pin[nf + 1].data_ptr(),
                                   pin[nf + 2].data_ptr() if nf == 3 else None)
     dt = time.perf_counter() - t0
     lbm._check(code, "lbm_moments", allow_unstable=True)
     return {"value": n * args.steps / dt / 1e9, "unit": "GLUPS",
             "h2d_bytes_per_step": nf * 8 * n / args.steps,
-            "d2h_bytes_per_step": nf * 8 * n / args.steps,
-            "note": "lbm_init from pinned host arrays + lbm_step(K) + lbm_moments to pinned host"}
+            "d2h_bytes_per_step": (nf * 8 * n + chunks * 3 * 8 * count) / args.steps,
+            "note": "lbm_init from pinned host arrays + lbm_step(K) with lbm_conservation to the "
+                    "host every %d steps + lbm_moments to pinned host" % CONS_EVERY}
 
 
 def fp64_plain_leg(collision: str, steps: int = 20):

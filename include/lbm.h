@@ -277,14 +277,15 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
 
 /* Launch shape in use: out[0] = nodes per thread, out[1] = tile width in
  * thread chunks, out[2] = tile height in rows, out[3] = grid size (CTAs),
- * out[4] = kernel kind (0: register-chunk kernel; 1: TMA-staged D2Q9 kernel
- * with large tiles, 2048 nodes for 2-byte storage or 1024 for FP32, on a
- * two-stage ring, 256 threads; 2: the same kernel with small tiles, 1024 /
- * 512 nodes, on a three-stage ring; 3: wide CTAs of 320 threads with 2560 /
- * 1280-node tiles on a two-stage ring; 4: a deep ring, one CTA of 512
- * threads per SM with 2048 / 1024-node tiles on four stages.  For kinds 1
+ * out[4] = kernel kind (0: register-chunk kernel; 1 to 4: the TMA-staged
+ * D2Q9 kernel, whose CTAs have one warp that only moves tiles in and out
+ * besides the colliding warps.  1: large tiles, 8-warp CTAs, 1792 nodes for
+ * 2-byte storage or 896 for FP32, two-stage ring; 2: small tiles, 8-warp
+ * CTAs, 896 / 448 nodes, three-stage ring; 3: 10-warp CTAs, 2304 / 1152
+ * nodes, two-stage ring; 4: deep ring, one 16-warp CTA per SM, 1920 / 960
+ * nodes, four stages.  For kinds 1
  * to 4 the tile width is 64/128/256 nodes chosen per instance (at most
- * 32 tile nodes / threads) and out[1], out[2] are 0; tiles go in and out of
+ * 32 tile nodes / colliding threads) and out[1], out[2] are 0; tiles go in and out of
  * shared memory by TMA).  Selection: the create-time
  * autotuner (median of three timed launches per candidate shape; the choice
  * is cached per device, lattice, types, rule, boundary and instance sizes

@@ -324,7 +324,7 @@ int apply_shape(lbm_ctx* ctx, const Shape& s) {
     LBM_CK(cudaMemcpyAsync(ctx->d_inst, ctx->layout.inst.data(), sizeof(InstDesc) * ctx->count,
                            cudaMemcpyHostToDevice, ctx->stream));
     LBM_CK(cudaStreamSynchronize(ctx->stream));
-    const int block = s.kind >= 1 ? smem_threads(s.kind - 1) : s.tw * s.th;
+    const int block = s.kind >= 1 ? smem_block_threads(s.kind - 1) : s.tw * s.th;
     int per_sm = 0;
     LBM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     per_sm = std::max(per_sm, 1);
@@ -420,7 +420,7 @@ StepArgs step_args(const lbm_ctx* ctx, int src) {
 cudaError_t launch_step(lbm_ctx* ctx, int src, cudaStream_t s) {
     StepArgs a = step_args(ctx, src);
     void* params[] = {&a};
-    const int block = ctx->shape.kind >= 1 ? smem_threads(ctx->shape.kind - 1)
+    const int block = ctx->shape.kind >= 1 ? smem_block_threads(ctx->shape.kind - 1)
                                            : ctx->shape.tw * ctx->shape.th;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

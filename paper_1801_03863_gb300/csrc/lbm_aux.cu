@@ -250,20 +250,27 @@ __device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, 
 // Conservation, pass 1: the block of work item (i, b) sums (sum d,
 // sum d v_x, sum d v_y) of f(t_n) over the rows y = b mod P_i of instance i
 // (P_i = cons_partials(ny_i)); thread t takes x = t, t + CONS_THREADS, ...
-// of each of those rows, rows in increasing order, and the block reduces
+// of each of those rows, rows in increasing order (issuing the loads of a
+// few of its nodes of a row together, adding them in order), and the block
+// reduces
 // its threads in a fixed tree into partials[(i*CONS_PARTIALS + b)*3 + c].
 // The order is fixed by the instance alone.  The sums run in FP64, except
 // for FP16 storage, where they are exact integers: every FP16 value is a
 // multiple of 2^-24 below 2^16 in magnitude, so 2^24 d is an integer below
 // 2^40, and a thread's nodes add exactly in 64-bit integers, converted to
 // FP64 once (a node with a non-finite value takes the FP64 path, so that it
-// propagates).  Interior nodes pull with plain shifted
+// propagates); nodes whose values are all below 8 in magnitude, which is
+// every node of a physical state, sum in 32-bit integers first, without
+// 64-bit conversions.  Interior nodes pull with plain shifted
 // loads; the outer ring applies the boundary rules.
 template <class Lat, typename S>
-__global__ void __launch_bounds__(CONS_THREADS)
+__global__ void __launch_bounds__(CONS_THREADS, CONS_MIN_BLOCKS)
 cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool pulled,
                     double* partials) {
     using V = typename std::conditional<sizeof(S) == 2, float, double>::type;
+    // nodes x, x + T, ..., x + (K - 1) T of a row (T = CONS_THREADS) whose
+    // loads a thread issues together before it adds them in order
+    constexpr int K = sizeof(S) == 8 ? 2 : 4;
     __shared__ double sh[3][CONS_THREADS];
     const int2 it = items[blockIdx.x];
     const InstDesc in = insts[it.x];
@@ -273,15 +280,31 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
     long long i0 = 0, i1 = 0, i2 = 0;  // FP16: exact sums in units of 2^-24
     for (int y = it.y; y < ny; y += P) {
         const bool yint = Lat::Q == 3 || (y >= 1 && y <= ny - 2);
-        for (int x = threadIdx.x; x < nx; x += CONS_THREADS) {
+        for (int x0 = threadIdx.x; x0 < nx; x0 += K * CONS_THREADS) {
+          S raw[K][Lat::Q];
+          uint32_t plain = 0u;  // bit k: node k is read with plain shifted loads
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+              const int x = x0 + k * CONS_THREADS;
+              if (x < nx && (!pulled || (yint && x >= 1 && x <= nx - 2))) {
+                  plain |= 1u << k;
+#pragma unroll
+                  for (int a = 0; a < Lat::Q; ++a) {
+                      const int sx = pulled ? x - Lat::vx(a) : x, sy = pulled ? y - Lat::vy(a) : y;
+                      raw[k][a] = base[(int64_t)a * in.plane + (int64_t)sy * in.pitch + sx];
+                  }
+              }
+          }
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int x = x0 + k * CONS_THREADS;
+            if (x >= nx) break;
             V d[Lat::Q];
-            if (!pulled || (yint && x >= 1 && x <= nx - 2)) {
+            if ((plain >> k) & 1u) {
 #pragma unroll
                 for (int a = 0; a < Lat::Q; ++a) {
-                    const int sx = pulled ? x - Lat::vx(a) : x, sy = pulled ? y - Lat::vy(a) : y;
-                    const S v = base[(int64_t)a * in.plane + (int64_t)sy * in.pitch + sx];
-                    if constexpr (sizeof(S) == 2) d[a] = Store<S>::to_f32(v);
-                    else d[a] = Store<S>::to_f64(v);
+                    if constexpr (sizeof(S) == 2) d[a] = Store<S>::to_f32(raw[k][a]);
+                    else d[a] = Store<S>::to_f64(raw[k][a]);
                 }
             } else if constexpr (sizeof(S) == 2) {
                 node_state_f32<Lat, S>(src, in, x, y, pulled, d);
@@ -290,21 +313,41 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
             }
             bool exact = false;
             if constexpr (std::is_same<S, __half>::value) {
-                long long r0 = 0, r1 = 0, r2 = 0;
-                bool finite = true;
+                // every |d| < 8: 2^24 d below 2^27, the node sums of nine
+                // such terms below 2^31, in 32-bit integers
+                bool small = true;
 #pragma unroll
-                for (int a = 0; a < Lat::Q; ++a) {
-                    finite = finite && (fabsf(d[a]) <= 65504.f);
-                    const long long v = __float2ll_rn(d[a] * 16777216.f);  // 2^24 d, exact
-                    r0 += v;
-                    if (Lat::vx(a) != 0) r1 += Lat::vx(a) > 0 ? v : -v;
-                    if (Lat::vy(a) != 0) r2 += Lat::vy(a) > 0 ? v : -v;
-                }
-                if (finite) {
+                for (int a = 0; a < Lat::Q; ++a) small = small && (fabsf(d[a]) < 8.f);
+                if (small) {
+                    int r0 = 0, r1 = 0, r2 = 0;
+#pragma unroll
+                    for (int a = 0; a < Lat::Q; ++a) {
+                        const int v = __float2int_rn(d[a] * 16777216.f);  // 2^24 d, exact
+                        r0 += v;
+                        if (Lat::vx(a) != 0) r1 += Lat::vx(a) > 0 ? v : -v;
+                        if (Lat::vy(a) != 0) r2 += Lat::vy(a) > 0 ? v : -v;
+                    }
                     i0 += r0;
                     i1 += r1;
                     i2 += r2;
                     exact = true;
+                } else {
+                    long long r0 = 0, r1 = 0, r2 = 0;
+                    bool finite = true;
+#pragma unroll
+                    for (int a = 0; a < Lat::Q; ++a) {
+                        finite = finite && (fabsf(d[a]) <= 65504.f);
+                        const long long v = __float2ll_rn(d[a] * 16777216.f);
+                        r0 += v;
+                        if (Lat::vx(a) != 0) r1 += Lat::vx(a) > 0 ? v : -v;
+                        if (Lat::vy(a) != 0) r2 += Lat::vy(a) > 0 ? v : -v;
+                    }
+                    if (finite) {
+                        i0 += r0;
+                        i1 += r1;
+                        i2 += r2;
+                        exact = true;
+                    }
                 }
             }
             if (!exact) {
@@ -316,6 +359,7 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
                     if (Lat::vy(a) != 0) s2 += Lat::vy(a) * v;
                 }
             }
+          }
         }
     }
     if constexpr (std::is_same<S, __half>::value) {

@@ -12,7 +12,8 @@ namespace lbm {
 // one block of CONS_THREADS threads; the split is a function of the instance
 // alone, so the FP64 summation order never depends on the device.
 constexpr int CONS_PARTIALS = 64;
-constexpr int CONS_THREADS = 1024;
+constexpr int CONS_THREADS = 256;
+constexpr int CONS_MIN_BLOCKS = 3;  // resident blocks per SM the register budget aims at
 __host__ __device__ inline int cons_partials(int ny) { return ny < CONS_PARTIALS ? ny : CONS_PARTIALS; }
 
 enum class AuxOp { Init, SetF, CollideInPlace, Moments, GatherF, Conservation };
@@ -62,46 +63,35 @@ const void* step_kernel_bf16(int lattice, int collision, int V);
 const void* step_kernel_smem_f32(int collision, int variant, size_t* smem_bytes);
 const void* step_kernel_smem_f16(int collision, int variant, size_t* smem_bytes);
 const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes);
-// Tile geometry of those kernels: nodes per tile for a storage type, and
-// the tile width for an instance of width nx.
-#ifndef LBM_SMEM_TILE2
-#define LBM_SMEM_TILE2 2048
-#endif
-#ifndef LBM_SMEM_TILE4
-#define LBM_SMEM_TILE4 1024
-#endif
-#ifndef LBM_SMEM_TILE2_SMALL
-#define LBM_SMEM_TILE2_SMALL 1024
-#endif
-#ifndef LBM_SMEM_TILE4_SMALL
-#define LBM_SMEM_TILE4_SMALL 512
-#endif
-#ifndef LBM_SMEM_TILE2_WIDE
-#define LBM_SMEM_TILE2_WIDE 2560
-#endif
-#ifndef LBM_SMEM_TILE4_WIDE
-#define LBM_SMEM_TILE4_WIDE 1280
-#endif
-// Geometries of the TMA-staged kernel (variant = launch-shape kind - 1):
-//   0  large tiles: 2048 nodes (2-byte storage) / 1024 (FP32), 256 threads,
-//      two-stage ring (fewer per-tile costs, for arithmetic-bound rules);
-//   1  small tiles: 1024 / 512 nodes, 256 threads, three-stage ring (more
-//      copies in flight, for bandwidth-bound rules);
-//   2  wide CTAs: 2560 / 1280 nodes, 320 threads (ten warps), two-stage
-//      ring: two CTAs give 20 warps per SM instead of 16, at a register
-//      budget of 102 per thread;
-//   3  deep ring: one CTA per SM of 512 threads (16 warps) with 2048 /
-//      1024-node tiles on a four-stage ring, so a stage is refilled three
-//      tiles before it is needed.
+// Geometries of the TMA-staged kernel (variant = launch-shape kind - 1).
+// Every CTA has one copy warp, which writes finished tiles out and issues
+// the copies of the next ones, besides its colliding warps; a tile holds
+// 64 nodes per unit x the units of each colliding warp:
+//   0  large tiles: 8 warps, 7 colliding with 4 units each (2-byte storage;
+//      2 for FP32): 1792 / 896 nodes, two-stage ring;
+//   1  small tiles: 8 warps, 2 / 1 units each: 896 / 448 nodes, three-stage
+//      ring (more copies in flight per node);
+//   2  wide CTAs: 10 warps, 4 / 2 units each: 2304 / 1152 nodes, two stages;
+//   3  deep ring: one CTA of 16 warps per SM, 2 / 1 units each: 1920 / 960
+//      nodes on a four-stage ring, so a stage is refilled three tiles before
+//      it is needed.
+// Two CTAs of the 8- and 10-warp geometries fit an SM (registers and
+// shared memory); the 16-warp one keeps all 128 registers per thread.
 #ifndef LBM_SMEM_STAGES_DEEP
 #define LBM_SMEM_STAGES_DEEP 4
 #endif
-inline int smem_tile_nodes(int storage, int variant) {
-    if (variant == 1) return storage == 1 ? LBM_SMEM_TILE4_SMALL : LBM_SMEM_TILE2_SMALL;
-    if (variant == 2) return storage == 1 ? LBM_SMEM_TILE4_WIDE : LBM_SMEM_TILE2_WIDE;
-    return storage == 1 ? LBM_SMEM_TILE4 : LBM_SMEM_TILE2;
+// colliding threads of a CTA (the copy warp comes on top)
+constexpr int smem_threads(int variant) {
+    return variant == 2 ? 288 : (variant == 3 ? 480 : 224);
 }
-inline int smem_threads(int variant) { return variant == 2 ? 320 : (variant == 3 ? 512 : 256); }
+constexpr int smem_block_threads(int variant) { return smem_threads(variant) + 32; }
+// units of 32 node pairs per colliding warp and tile (storage 1: FP32)
+constexpr int smem_units(int storage, int variant) {
+    return (variant == 0 || variant == 2 ? 4 : 2) / (storage == 1 ? 2 : 1);
+}
+constexpr int smem_tile_nodes(int storage, int variant) {
+    return 64 * smem_units(storage, variant) * (smem_threads(variant) / 32);
+}
 // Tile width: 64, 128 or 256 nodes by the instance width, at most
 // 32 tile_nodes / threads, so that each warp's units (tile_nodes /
 // (2 threads) units of 64 nodes) cover whole tile rows.

@@ -4,13 +4,12 @@
 // Same time step as step_kernel (pull-stream + collide + boundary rules of
 // Sec. IV.F, Eq. 2), organised around the Tensor Memory Accelerator:
 //
-//  * A CTA (256 threads) walks the tile table of the context; a tile is X
-//    nodes (64, 128 or 256, chosen per instance) by R = TILE_NODES / X rows.
-//    Two geometries are compiled: large tiles (2048 nodes for 2-byte storage,
-//    1024 for 4-byte) with a two-stage ring, which halve the per-tile costs
-//    of arithmetic-bound rules, and small tiles (1024 / 512) with a
-//    three-stage ring, which keep more copies in flight for bandwidth-bound
-//    ones; the autotuner picks per context.
+//  * A CTA walks the tile table of the context; a tile is X nodes (64, 128
+//    or 256, chosen per instance) by R = TILE_NODES / X rows.  Four
+//    geometries are compiled (smem_tile_nodes): 8-warp CTAs with large or
+//    small tiles on two- or three-stage rings, 10-warp CTAs, and one
+//    16-warp CTA per SM on a four-stage ring; the autotuner picks per
+//    context.
 //  * Each instance's populations are described to TMA as a 3-D tensor
 //    (x < nx, row, plane).  Every copy starts at an x that is a multiple of
 //    16 bytes (tiles start at multiples of 64 nodes, halo chunks 16 bytes
@@ -22,22 +21,22 @@
 //    zero-filled by the hardware, which is exactly the cavity's "outside"
 //    value (deviation 0).
 //  * A ring of STAGES shared-memory stages, each with a "full" mbarrier (the
-//    copies landed) and an "empty" one (every warp is done with it): the
-//    copies of the next tiles are in flight while one is collided.  No warp
-//    is a dedicated producer: thread 0 fills every stage at the start, and
-//    afterwards the last warp to finish a tile (a per-stage counter tells
-//    which) writes it out and refills the stage with the tile NS later at
-//    once, so a free stage never waits for one particular warp.
-//  * Each warp owns whole rows of the tile and takes them in units of 32
-//    node pairs (one pair per lane, packed FP32x2 arithmetic), left to right.
-//    A unit writes its post-collision pairs back over its own positions in
-//    the stage once every lane has read them; the one value a later unit
-//    still needs from an overwritten position (the pair left of the next
-//    unit's first node) is parked beforehand in the unused words of the
-//    halo chunk.  When every warp is done with a tile, the last one writes
-//    the stage's nine planes out with one tensor store each (rows and
-//    chunks beyond the lattice are clipped by the hardware) and waits for
-//    TMA to have read them before it refills the stage.
+//    copies landed) and an "empty" one (every colliding warp is done with
+//    it).  One warp of the CTA only moves data: it fills every stage at the
+//    start, and whenever the colliding warps are done with a tile it writes
+//    the stage's nine planes out with one tensor store each (rows and chunks
+//    beyond the lattice are clipped by the hardware), waits for TMA to have
+//    read them and refills the stage with the tile NS later.  Issuing those
+//    26 copies takes a few thousand cycles per tile; a colliding warp that
+//    did it (as the last one to finish a tile) fell behind every time and
+//    held the whole CTA back.
+//  * Each colliding warp owns whole rows of the tile and takes them in units
+//    of 32 node pairs (one pair per lane, packed FP32x2 arithmetic), left to
+//    right.  A unit writes its post-collision pairs back over its own
+//    positions in the stage once every lane has read them; the one value a
+//    later unit still needs from an overwritten position (the pair left of
+//    the next unit's first node) is parked beforehand in the unused words of
+//    the halo chunk.
 //  * Every mbarrier wait is bounded; on timeout the kernel records an error
 //    word and each warp leaves after a bounded wait for the CTA's copies
 //    still in flight.
@@ -60,8 +59,9 @@ namespace lbm {
 #define LBM_SMEM_STAGES_SMALL 3  // ring depth, small tiles
 #endif
 
-template <typename S, int TILE = (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4),
-          int NST = LBM_SMEM_STAGES, int NTHREADS = 256>
+// TILE nodes per tile, NST stages, NTHREADS colliding threads (the copy
+// warp comes on top)
+template <typename S, int TILE, int NST, int NTHREADS>
 struct SmemTile {
     static constexpr int E = 16 / (int)sizeof(S);  // elements per 16-byte chunk
     static constexpr int TILE_NODES = TILE;        // X * R
@@ -86,10 +86,10 @@ struct SmemTile {
     static constexpr size_t PARAMS_OFF = STAGES_BYTES;
     static constexpr size_t PARAMS_BYTES = 256;  // per stage
     static constexpr size_t BARS_OFF = PARAMS_OFF + PARAMS_BYTES * STAGES;
-    // two mbarriers per stage, then one warp counter per stage and the
-    // count of tiles whose copies were issued
+    // two mbarriers per stage, then the count of tiles whose copies were
+    // issued
     static constexpr size_t COUNT_OFF = BARS_OFF + 16 * STAGES;
-    static constexpr size_t SMEM_BYTES = 128 + COUNT_OFF + 4 * STAGES + 16;
+    static constexpr size_t SMEM_BYTES = 128 + COUNT_OFF + 16;
     static_assert(UNITS >= 1 && UNITS <= 4, "a unit's halo chunk parks at most 3 values");
     static_assert(TILE_NODES % (2 * THREADS) == 0, "whole units per warp");
     static_assert(HALO_OFF % 128 == 0 && PLANE_BYTES % 128 == 0,
@@ -309,7 +309,7 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
 // following packed add, and it does so alike wherever the collision is
 // inlined, which scalar code would not reproduce.
 template <typename S, int COLL, int TILE, int NST, int NTHREADS>
-__global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBLOCKS)
+__global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_SMEM_MINBLOCKS)
     step_kernel_smem(const StepArgs args) {
     using TS = SmemTile<S, TILE, NST, NTHREADS>;
     constexpr int E = TS::E;
@@ -348,12 +348,9 @@ __global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBL
     }
     __syncthreads();
 
-    unsigned int* done = reinterpret_cast<unsigned int*>(smem_al + TS::COUNT_OFF);
-    volatile int* filled = reinterpret_cast<volatile int*>(done + NS);  // tiles filled so far
-    if (tid == 0) {
-        for (int k = 0; k < NS; ++k) done[k] = 0u;
-        *filled = 0;
-    }
+    // tiles whose copies the copy warp has issued (read on the failure path)
+    volatile int* filled = reinterpret_cast<volatile int*>(smem_al + TS::COUNT_OFF);
+    if (tid == 0) *filled = 0;
 
     // Local tile j out of its stage (every warp is done with it): one
     // tensor store per plane, then a commit.
@@ -372,7 +369,7 @@ __global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBL
     // stage takes next), all on the stage's full barrier.
     auto fill = [&](int j, const TileDesc tile) {
         const int st = j % NS;
-        atomicMax((int*)filled, j + 1);
+        *filled = j + 1;
         // test hook of the timeout path: the copies of one chosen tile are
         // never issued, so its full barrier never completes
         if ((int)blockIdx.x + j * G == args.lost_tile) return;
@@ -411,9 +408,38 @@ __global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBL
     wait_previous_grid();
     allow_next_grid();
     __syncthreads();  // counters initialised
-    // thread 0 fills every stage with the CTA's first tiles
-    if (tid == 0) {
-        for (int j = 0; j < min(NS, ntl); ++j) fill(j, args.tiles[blockIdx.x + j * G]);
+    if (warp == TS::WARPS) {
+        // The copy warp (its lane 0): fill every stage with the CTA's first
+        // tiles; then, once every colliding warp is done with tile j, write
+        // it out and refill its stage with tile j + NS.
+        if (lane == 0) {
+            for (int t = 0; t < min(NS, ntl); ++t) fill(t, args.tiles[blockIdx.x + t * G]);
+            int jp = 0;
+            bool pfail = false;
+            for (; jp < ntl; ++jp) {
+                const int st = jp % NS;
+                if (!mbar_wait_bounded(&empty[st], (uint32_t)((jp / NS) & 1), args.spin_limit)) {
+                    pfail = true;
+                    break;
+                }
+                store_tile(jp);
+                if (jp + NS < ntl) {
+                    const TileDesc nt = params[st].next;
+                    bulk_wait_read();  // the stores have read the stage
+                    fill(jp + NS, nt);
+                }
+            }
+            if (pfail) {
+                // the colliding warps gave up on a tile: report it, and give
+                // the copies still in flight a bounded chance to land
+                atomicOr(args.error, 1u);
+                const int nf = *filled;
+                for (int t = jp; t < nf; ++t)
+                    mbar_wait_bounded(&full[t % NS], (uint32_t)((t / NS) & 1), args.spin_limit);
+            }
+            bulk_wait_all();  // no shared-memory reads left behind
+        }
+        return;
     }
 
     // Each warp collides its units of a tile, then its lane 0 arrives on the
@@ -568,25 +594,7 @@ __global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBL
         // this thread's stage writes come before the tensor stores that read them
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-            mbar_arrive(&empty[st]);  // this warp is done with the stage
-            if (atomicAdd(&done[st], 1u) == TS::WARPS - 1) {
-                // last warp of the tile: every other warp has arrived (the
-                // bounded wait gives the acquire), so write the tile out
-                done[st] = 0u;
-                if (!mbar_wait_bounded(&empty[st], (uint32_t)((j / NS) & 1), args.spin_limit)) {
-                    fail = true;
-                } else {
-                    store_tile(j);
-                    if (j + NS < ntl) {
-                        const TileDesc nt = params[st].next;
-                        bulk_wait_read();  // the stores have read the stage
-                        fill(j + NS, nt);
-                    }
-                }
-            }
-        }
-        fail = __shfl_sync(0xffffffffu, fail, 0);
+        if (lane == 0) mbar_arrive(&empty[st]);  // the copy warp takes it from here
     }
     if (fail) {
         // a copy or a stage release never came: report it and give the
@@ -599,8 +607,6 @@ __global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBL
                 mbar_wait_bounded(&full[t % NS], (uint32_t)((t / NS) & 1), args.spin_limit);
         }
     }
-    // stores issued by this thread leave no shared-memory reads behind
-    if (lane == 0) bulk_wait_all();
 }
 
 // The TMA-staged D2Q9 kernel for a collision rule and tile geometry VARIANT
@@ -609,12 +615,10 @@ __global__ void __launch_bounds__(NTHREADS, NTHREADS >= 512 ? 1 : LBM_SMEM_MINBL
 // *smem_bytes receives its dynamic shared memory size.
 template <typename S, int VARIANT>
 const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
-    constexpr int TN = VARIANT == 1 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2_SMALL : LBM_SMEM_TILE4_SMALL)
-                     : VARIANT == 2 ? (sizeof(S) == 2 ? LBM_SMEM_TILE2_WIDE : LBM_SMEM_TILE4_WIDE)
-                                    : (sizeof(S) == 2 ? LBM_SMEM_TILE2 : LBM_SMEM_TILE4);
+    constexpr int TN = smem_tile_nodes(sizeof(S) == 4 ? 1 : 2, VARIANT);  // 1: FP32 storage
     constexpr int NS = VARIANT == 1 ? LBM_SMEM_STAGES_SMALL
                      : VARIANT == 3 ? LBM_SMEM_STAGES_DEEP : LBM_SMEM_STAGES;
-    constexpr int NT = VARIANT == 2 ? 320 : (VARIANT == 3 ? 512 : 256);
+    constexpr int NT = smem_threads(VARIANT);
     using TS = SmemTile<S, TN, NS, NT>;
     *smem_bytes = TS::SMEM_BYTES;
     switch (collision) {

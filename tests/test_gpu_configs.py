@@ -143,8 +143,8 @@ def _fp16_one_step_bound(fo, n_nodes):
 @pytest.mark.parametrize("shape", ["smem", "smems", "smemw", "smemd"])
 def test_cavity_ensemble_64_one_step_and_conservation(shape, monkeypatch):
     """Config: 64 cavities, FP32 compute, FP16 storage, on the TMA-staged
-    kernel with large ("smem") and small ("smems") tiles and wide CTAs
-    ("smemw").  One step of every
+    kernel with large ("smem") and small ("smems") tiles, 10-warp CTAs
+    ("smemw") and the deep ring ("smemd").  One step of every
     node of seven instances against the oracle (from the GPU state): the four
     smallest (side 64: every 64-node unit touches a wall), the two largest
     (1024^2: almost every unit takes the interior fast path) and one whose

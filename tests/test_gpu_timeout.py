@@ -25,7 +25,7 @@ def _cavity(nx, ny):
 @pytest.mark.parametrize("shape,lost", [("smem", 5), ("smem", 0), ("smems", 3), ("smemw", 4),
                                                ("smemd", 6)])
 def test_lost_copy_times_out_and_is_reported(shape, lost, monkeypatch):
-    nx, ny = 256, 64  # 8 large tiles, 16 small ones, 7 of the wide CTAs' 2560 nodes
+    nx, ny = 256, 64  # 10 large tiles, 20 small ones, 8 of the 10-warp CTAs', 10 deep-ring ones
     monkeypatch.setenv("LBM_SHAPE", shape)
     monkeypatch.setenv("LBM_SPIN_LIMIT", "65536")
     monkeypatch.setenv("LBM_TEST_LOST_TILE", str(lost))
