@@ -45,7 +45,7 @@ Shape default_shape(int lattice, int storage) {
 }
 
 // Launch-shape candidates of the autotuner.  D2Q9 with FP32 arithmetic: the
-// TMA-staged kernel in both tile geometries and the default register-chunk
+// TMA-staged kernel in its four geometries and the default register-chunk
 // shape (which wins only on small, cache-resident lattices).  D1Q3 and the
 // FP64 path: register-chunk shapes, V = the compiled widths of the storage
 // type, tiles of 128 or 256 threads.
