@@ -225,32 +225,35 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     constexpr double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
     // Moments of the pulled state (Sec. II.A) and the stress moments
-    // M8 = sum f (v_x^2 - v_y^2), M9 = sum f v_x v_y (rows 8, 9 of T).
-    const T drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    // M8 = sum f (v_x^2 - v_y^2), M9 = sum f v_x v_y (rows 8, 9 of T), from
+    // the sums of opposite populations.
+    const T n13 = d[1] + d[3], n24 = d[2] + d[4], n57 = d[5] + d[7], n68 = d[6] + d[8];
+    const T drho = (d[0] + (n13 + n24)) + (n57 + n68);
     const T a57 = d[5] - d[7], a86 = d[8] - d[6];
     const T jx = (d[1] - d[3]) + a57 + a86;
     const T jy = (d[2] - d[4]) + a57 - a86;
-    const T pxx = (d[1] + d[3]) - (d[2] + d[4]);
-    const T pxy = (d[5] + d[7]) - (d[6] + d[8]);
+    const T pxx = n13 - n24;
+    const T pxy = n57 - n68;
     const T rho = rho0 + drho;
     const T ir = N::rcp(rho);
     const T ux = jx * ir, uy = jy * ir;
-    const T uxx = ux * ux, uyy = uy * uy;
+    const T uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const T U2 = uxx + uyy, D2 = uxx - uyy;
     // Non-equilibrium stress relaxed at 1/tau (Eqs. discreteviscoconst/isoconst):
     // c8 - M8eq = (1 - omega)(M8pre - M8eq), likewise for M9; scaled by 1/(4 W).
     const T k = (T(1.0) - omega) * T(0.25);
-    const T c8 = (T(9.0) * k) * N::mad(pxx, ir, uyy - uxx);
-    const T c9 = (T(36.0) * k) * N::mad(pxy, ir, -(ux * uy));
-    // delta_a = p^start_a / W_a - 1 = (even part s) +- 3 (odd part h)
-    const T C1 = T(1.0), C3 = T(3.0), C45 = T(4.5);
-    const T b0 = T(-1.5) * (uxx + uyy);
-    const T sx = N::mad(C45, uxx, b0 + c8);
-    const T sy = N::mad(C45, uyy, b0 - c8);
-    const T sp_ = ux + uy, dm_ = uy - ux;
-    const T sp = N::mad(C45 * sp_, sp_, b0 + c9);
-    const T sm = N::mad(C45 * dm_, dm_, b0 - c9);
+    const T c8 = (T(9.0) * k) * N::mad(pxx, ir, -D2);
+    const T c9 = (T(36.0) * k) * N::mad(pxy, ir, -uxy);
+    // delta_a = p^start_a / W_a - 1 = (even part s) +- 3 (odd part h), the
+    // even parts written with U2 = |u|^2:
+    //   s_0 = -3/2 U2,  s_x,y = 3/4 U2 +- G,  s_+,- = 3 U2 +- P,
+    //   G = 9/4 (u_x^2 - u_y^2) + c8,  P = 9 u_x u_y + c9.
+    const T G = N::mad(T(2.25), D2, c8);
+    const T P = N::mad(T(9.0), uxy, c9);
+    const T C1 = T(1.0), C3 = T(3.0);
     // coefficients of the terms odd in v: 3 v.u, plus for MinxEnt2 the
     // relaxed heat flux, T_5a g_x / (12 W_a) = (-3/2 on +x, +3 on (+,+) ...)
+    const T sp_ = ux + uy, dm_ = uy - ux;
     T hx = ux, hy = uy, lp = sp_, lm = dm_;
     if constexpr (NFREE == 2) {
         // q^pre - q^eq = -Q with Q_x = (d1 - d3) - 2 (a57 + a86) (deviation
@@ -268,9 +271,14 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     // exist (reading C-NEG).  cx .. cm: the even parts 1 + s of the opposite
     // pairs (the mean of y_a and y_opp(a)).
     T del[9], y[9];
-    const T cx = C1 + sx, cy = C1 + sy, cp = C1 + sp, cm = C1 + sm;
+    T cx, cy, cp, cm;
     if constexpr (YFORM) {
-        y[0] = C1 + b0;
+        const T F = N::mad(T(0.75), U2, C1), E = N::mad(C3, U2, C1);
+        cx = F + G;
+        cy = F - G;
+        cp = E + P;
+        cm = E - P;
+        y[0] = N::mad(T(-1.5), U2, C1);
         y[1] = N::mad(C3, hx, cx);
         y[3] = N::mad(-C3, hx, cx);
         y[2] = N::mad(C3, hy, cy);
@@ -280,7 +288,9 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         y[6] = N::mad(C3, lm, cm);
         y[8] = N::mad(-C3, lm, cm);
     } else {
-        del[0] = b0;
+        const T F0 = T(0.75) * U2, E0 = C3 * U2;
+        const T sx = F0 + G, sy = F0 - G, sp = E0 + P, sm = E0 - P;
+        del[0] = T(-1.5) * U2;
         del[1] = N::mad(C3, hx, sx);
         del[3] = N::mad(-C3, hx, sx);
         del[2] = N::mad(C3, hy, sy);
@@ -291,6 +301,10 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         del[8] = N::mad(-C3, lm, sm);
 #pragma unroll
         for (int a = 0; a < 9; ++a) y[a] = C1 + del[a];
+        cx = C1 + sx;
+        cy = C1 + sy;
+        cp = C1 + sp;
+        cm = C1 + sm;
     }
     // FP64: the exact test of reading C-NEG.  FP32: see the Newton-step test below.
     typename N::Pred ok{};
@@ -451,39 +465,61 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
             }
         }
     }
-    // (T^T s~)_a from the scaled solution (sps, sx_, sy_ hold twice s~_eps,
-    // s~_x, s~_y)
-    T t[9];
-    const T ce = -(se + sps);
-    const T cd = N::mad(T(0.5), sps, se + se);
-    t[0] = N::mad(T(-4.0), se, sps + sps);
-    if constexpr (NFREE == 4) {
-        const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
-        t[1] = ce - sx_;
-        t[3] = ce + sx_;
-        t[2] = ce - sy_;
-        t[4] = ce + sy_;
-        t[5] = N::mad(T(0.5), pxy_, cd);
-        t[7] = N::mad(T(-0.5), pxy_, cd);
-        t[6] = N::mad(T(-0.5), mxy_, cd);
-        t[8] = N::mad(T(0.5), mxy_, cd);
-    } else {
-        t[1] = t[2] = t[3] = t[4] = ce;
-        t[5] = t[6] = t[7] = t[8] = cd;
-    }
-    // f^post_a = rho W_a (y_a - (T^T s~)_a); the 1/9 of A's scaling and the
-    // log base go into the last factor.
-    const T rs = rho * T(N::LOG_SCALE / 9.0);
+    // f^post_a = rho W_a (y_a - (T^T s~)_a), with the 1/9 of A's scaling and
+    // the log base L (Num::LOG_SCALE) in the factor of T^T s~; sps, sx_, sy_
+    // hold twice s~_eps, s~_x, s~_y.
     if constexpr (YFORM) {
-        T f[9];
+        // g_a = f^post_a / W_a = rho y_a - u_a, u_a = rho L (T^T s~)_a / (9 W_a):
+        // the solution is scaled by kappa = rho L once, and the class factors
+        // 1 / (9 W_a) = 1/4, 1, 4 (rest, axis, diagonal) go into constants.
+        const T kap = rho * T(N::LOG_SCALE);
+        const T Se = kap * se, Sp = kap * sps;
+        T u[9], g[9];
+        u[0] = N::mad(T(0.5), Sp, -Se);
+        const T CE = -(Se + Sp);
+        const T CD4 = N::mad(T(8.0), Se, Sp + Sp);
+        if constexpr (NFREE == 4) {
+            const T Sx = kap * sx_, Sy = kap * sy_;
+            const T pxy_ = Sx + Sy, mxy_ = Sx - Sy;
+            u[1] = CE - Sx;
+            u[3] = CE + Sx;
+            u[2] = CE - Sy;
+            u[4] = CE + Sy;
+            u[5] = N::mad(T(2.0), pxy_, CD4);
+            u[7] = N::mad(T(-2.0), pxy_, CD4);
+            u[6] = N::mad(T(-2.0), mxy_, CD4);
+            u[8] = N::mad(T(2.0), mxy_, CD4);
+        } else {
+            u[1] = u[2] = u[3] = u[4] = CE;
+            u[5] = u[6] = u[7] = u[8] = CD4;
+        }
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            f[a] = N::mad(-rs, t[a], (T(W[a]) * rho) * y[a]);
-            out[a] = f[a] - T(W[a]) * rho0;
+            g[a] = N::mad(rho, y[a], -u[a]);
+            out[a] = N::mad(T(W[a]), g[a], -(T(W[a]) * rho0));
         }
         if (rare) return lane_status<T>(ok, finite_nonneg<T, 9>(out, W, rho0));
-        return negative_status<T, 9>(f);
+        return negative_status<T, 9>(g);  // g_a has the sign of f^post_a
     } else {
+        T t[9];
+        const T ce = -(se + sps);
+        const T cd = N::mad(T(0.5), sps, se + se);
+        t[0] = N::mad(T(-4.0), se, sps + sps);
+        if constexpr (NFREE == 4) {
+            const T pxy_ = sx_ + sy_, mxy_ = sx_ - sy_;
+            t[1] = ce - sx_;
+            t[3] = ce + sx_;
+            t[2] = ce - sy_;
+            t[4] = ce + sy_;
+            t[5] = N::mad(T(0.5), pxy_, cd);
+            t[7] = N::mad(T(-0.5), pxy_, cd);
+            t[6] = N::mad(T(-0.5), mxy_, cd);
+            t[8] = N::mad(T(0.5), mxy_, cd);
+        } else {
+            t[1] = t[2] = t[3] = t[4] = ce;
+            t[5] = t[6] = t[7] = t[8] = cd;
+        }
+        const T rs = rho * T(N::LOG_SCALE / 9.0);
         // d^post_a = W_a (drho + rho delta_a) - rho (T^T s~)_a
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
