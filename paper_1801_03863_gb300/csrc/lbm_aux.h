@@ -80,14 +80,21 @@ const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes
 #ifndef LBM_SMEM_STAGES_DEEP
 #define LBM_SMEM_STAGES_DEEP 4
 #endif
+#ifndef LBM_DEEP_WARPS
+#define LBM_DEEP_WARPS 15  // colliding warps of the deep-ring CTA
+#endif
 // colliding threads of a CTA (the copy warp comes on top)
 constexpr int smem_threads(int variant) {
-    return variant == 2 ? 288 : (variant == 3 ? 480 : 224);
+    return variant == 2 ? 288 : (variant == 3 ? 32 * LBM_DEEP_WARPS : 224);
 }
 constexpr int smem_block_threads(int variant) { return smem_threads(variant) + 32; }
 // units of 32 node pairs per colliding warp and tile (storage 1: FP32)
+#ifndef LBM_DEEP_UNITS
+#define LBM_DEEP_UNITS 2  // units per colliding warp and tile of the deep ring (2-byte storage)
+#endif
 constexpr int smem_units(int storage, int variant) {
-    return (variant == 0 || variant == 2 ? 4 : 2) / (storage == 1 ? 2 : 1);
+    return (variant == 0 || variant == 2 ? 4 : (variant == 3 ? LBM_DEEP_UNITS : 2)) /
+           (storage == 1 ? 2 : 1);
 }
 constexpr int smem_tile_nodes(int storage, int variant) {
     return 64 * smem_units(storage, variant) * (smem_threads(variant) / 32);

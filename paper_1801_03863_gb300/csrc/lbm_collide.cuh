@@ -436,21 +436,24 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
         // MinxEnt2 tests the sign bits of every y; MinxEnt4 (whose quotients
         // catch a single negative population of a pair) tests y_0 and the
         // pair means c, which are negative when both of a pair are.
-        uint32_t neg[N::LANES];
+        // One integer word decides the common case: chk is +0 for a finite
+        // step (its bits are 0) and NaN otherwise, and the sign bits of the
+        // tested values are 0 when none is negative.
+        uint32_t neg[N::LANES], any = 0u;
 #pragma unroll
         for (int l = 0; l < N::LANES; ++l) {
-            neg[l] = 0u;
+            uint32_t sgn = 0u;
             if constexpr (LOGP && NFREE == 2) {
 #pragma unroll
-                for (int a = 0; a < 9; ++a) neg[l] |= __float_as_uint(N::lane(y[a], l));
-                neg[l] >>= 31;
+                for (int a = 0; a < 9; ++a) sgn |= __float_as_uint(N::lane(y[a], l));
             } else if constexpr (LOGP) {
-                neg[l] = (__float_as_uint(N::lane(cx, l)) | __float_as_uint(N::lane(cy, l)) |
-                          __float_as_uint(N::lane(cp, l)) | __float_as_uint(N::lane(cm, l))) >> 31;
+                sgn = __float_as_uint(N::lane(cx, l)) | __float_as_uint(N::lane(cy, l)) |
+                      __float_as_uint(N::lane(cp, l)) | __float_as_uint(N::lane(cm, l));
             }
+            neg[l] = sgn >> 31;
+            any |= (sgn & 0x80000000u) | __float_as_uint(N::lane(chk, l));
         }
-#pragma unroll
-        for (int l = 0; l < N::LANES; ++l) rare = rare || (N::lane(chk, l) != 0.f) || neg[l];
+        rare = any != 0u;
         if (rare) {
             if constexpr (N::LANES == 1) {
                 ok = N::lane(chk, 0) == 0.f && !neg[0];

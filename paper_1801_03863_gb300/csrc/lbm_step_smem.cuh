@@ -210,9 +210,11 @@ struct UnitGeom {
 // Pair of nodes (2p, 2p+1) of plane `pl` pulled with shift -VX in x, as
 // FP32x2.
 template <typename S, int VX>
-__device__ __forceinline__ float2 smem_pair(const unsigned char* pl, const UnitOffs& u) {
+__device__ __forceinline__ float2 smem_pair(const unsigned char* pl, const UnitOffs& u,
+                                            uint32_t* own_word = nullptr) {
     if constexpr (sizeof(S) == 2) {
         const uint32_t w0 = *reinterpret_cast<const uint32_t*>(pl + u.own);
+        if (own_word) *own_word = w0;
         uint32_t v;
         if constexpr (VX == 0) v = w0;
         else if constexpr (VX == 1)
@@ -235,31 +237,32 @@ __device__ __forceinline__ float2 smem_pair(const unsigned char* pl, const UnitO
     }
 }
 
-// The nine pulled values of one node pair.
+// The nine pulled values of one node pair, and the words to park (see
+// below): for 2-byte storage the pair's own words of planes 1, 5, 8, which
+// the pulls from x - 1 read anyway.
 template <typename S, int PB>
-__device__ __forceinline__ void load_unit(const unsigned char* st, const UnitOffs& u, F2 (&d)[9]) {
+__device__ __forceinline__ void load_unit(const unsigned char* st, const UnitOffs& u, F2 (&d)[9],
+                                          uint32_t (&pw)[3]) {
     d[0] = F2(smem_pair<S, 0>(st + 0 * PB, u));
-    d[1] = F2(smem_pair<S, 1>(st + 1 * PB, u));
+    d[1] = F2(smem_pair<S, 1>(st + 1 * PB, u, &pw[0]));
     d[2] = F2(smem_pair<S, 0>(st + 2 * PB, u));
     d[3] = F2(smem_pair<S, -1>(st + 3 * PB, u));
     d[4] = F2(smem_pair<S, 0>(st + 4 * PB, u));
-    d[5] = F2(smem_pair<S, 1>(st + 5 * PB, u));
+    d[5] = F2(smem_pair<S, 1>(st + 5 * PB, u, &pw[1]));
     d[6] = F2(smem_pair<S, -1>(st + 6 * PB, u));
     d[7] = F2(smem_pair<S, -1>(st + 7 * PB, u));
-    d[8] = F2(smem_pair<S, 1>(st + 8 * PB, u));
+    d[8] = F2(smem_pair<S, 1>(st + 8 * PB, u, &pw[2]));
+    if constexpr (sizeof(S) != 2) {
+        // 4-byte storage: the pair's second element is a word of its own
+        pw[0] = *reinterpret_cast<const uint32_t*>(st + 1 * PB + u.own + 4u);
+        pw[1] = *reinterpret_cast<const uint32_t*>(st + 5 * PB + u.own + 4u);
+        pw[2] = *reinterpret_cast<const uint32_t*>(st + 8 * PB + u.own + 4u);
+    }
 }
-
-// The word holding the pair's second element (2p + 1) in the planes pulled
-// from x - 1 (1, 5, 8): the value the next unit of the row pulls into its
-// first node.  For 2-byte storage it is the pair's own word, which
-// load_unit has just read.
 template <typename S, int PB>
-__device__ __forceinline__ void park_words(const unsigned char* st, const UnitOffs& u,
-                                           uint32_t (&w)[3]) {
-    const uint32_t at = u.own + (sizeof(S) == 2 ? 0u : 4u);
-    w[0] = *reinterpret_cast<const uint32_t*>(st + 1 * PB + at);
-    w[1] = *reinterpret_cast<const uint32_t*>(st + 5 * PB + at);
-    w[2] = *reinterpret_cast<const uint32_t*>(st + 8 * PB + at);
+__device__ __forceinline__ void load_unit(const unsigned char* st, const UnitOffs& u, F2 (&d)[9]) {
+    uint32_t pw[3];
+    load_unit<S, PB>(st, u, d, pw);
 }
 
 // Post-collision pair into the stage, over the lane's own position.
@@ -498,14 +501,13 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
                 const int sg = g.sg, x = g.x, y = g.y;
                 constexpr bool INTERIOR = decltype(interior_tag)::value;
                 CT d[Q];
-                load_unit<S, PB>(sb, uo, d);
+                uint32_t pw[3];
+                load_unit<S, PB>(sb, uo, d, pw);
                 // The next unit of the row pulls element x - 1 of its first
                 // pair from this unit's last pair, which this unit overwrites:
                 // park the word holding it (planes 1, 5, 8) in the row's halo
                 // chunk, word 3 - (sg + 1) (word 3 holds the left halo itself).
                 {
-                    uint32_t pw[3];
-                    park_words<S, PB>(sb, uo, pw);
                     if (lane == 31 && sg < smask) {
                         const uint32_t to = hrow + 4u * (uint32_t)(2 - sg);
                         *reinterpret_cast<uint32_t*>(sb + 1 * PB + to) = pw[0];
