@@ -73,12 +73,15 @@ const void* step_kernel_smem_bf16(int collision, int variant, size_t* smem_bytes
 //      ring (more copies in flight per node);
 //   2  wide CTAs: 10 warps, 4 / 2 units each: 2304 / 1152 nodes, two stages;
 //   3  deep ring: one CTA of 16 warps per SM, 2 / 1 units each: 1920 / 960
-//      nodes on a four-stage ring, so a stage is refilled three tiles before
-//      it is needed.
+//      nodes on a five- / four-stage ring, so a stage is refilled four /
+//      three tiles before it is needed.
 // Two CTAs of the 8- and 10-warp geometries fit an SM (registers and
 // shared memory); the 16-warp one keeps all 128 registers per thread.
 #ifndef LBM_SMEM_STAGES_DEEP
-#define LBM_SMEM_STAGES_DEEP 4
+#define LBM_SMEM_STAGES_DEEP 4   // FP32 storage
+#endif
+#ifndef LBM_SMEM_STAGES_DEEP2
+#define LBM_SMEM_STAGES_DEEP2 5  // 2-byte storage
 #endif
 #ifndef LBM_DEEP_WARPS
 #define LBM_DEEP_WARPS 15  // colliding warps of the deep-ring CTA

@@ -237,8 +237,8 @@ __device__ __forceinline__ uint32_t minxent_d2q9(const T (&d)[9], T rho0, const 
     const T rho = rho0 + drho;
     const T ir = N::rcp(rho);
     const T ux = jx * ir, uy = jy * ir;
-    const T uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
-    const T U2 = uxx + uyy, D2 = uxx - uyy;
+    const T uyy = uy * uy, uxy = ux * uy;
+    const T U2 = N::mad(ux, ux, uyy), D2 = N::mad(ux, ux, -uyy);  // |u|^2, u_x^2 - u_y^2
     // Non-equilibrium stress relaxed at 1/tau (Eqs. discreteviscoconst/isoconst):
     // c8 - M8eq = (1 - omega)(M8pre - M8eq), likewise for M9; scaled by 1/(4 W).
     const T k = (T(1.0) - omega) * T(0.25);

@@ -461,17 +461,17 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
             break;
         }
 
+        // what every unit needs; the boundary data (bc, strides, lid) is read
+        // by the edge units only
         const StageParams& p = params[st];
-        const int X = p.X;
-        const int x0 = p.x0, y0 = p.y0, nx = p.in.nx, ny = p.in.ny, bc = p.in.bc;
-        const int64_t pitch = p.in.pitch, plane = p.in.plane, off = p.in.off;
+        const int x0 = p.x0, y0 = p.y0, nx = p.in.nx, ny = p.in.ny;
         unsigned char* sb = reinterpret_cast<unsigned char*>(stage_base + (size_t)st * TS::STAGE_ELEMS);
-        const int sl2 = 25 - __clz(X);     // log2 of the units per tile row (X / 64)
+        const int lgX = 31 - __clz(p.X);   // log2 of the tile width X
+        const int sl2 = lgX - 6;           // log2 of the units per tile row (X / 64)
         const int smask = (1 << sl2) - 1;  // last unit of a row
         const Rates<CT> rates{CT(p.in.rates_f[0]), CT(p.in.rates_f[1]), CT(p.in.rates_f[2]),
                               CT(p.in.rates_f[3])};
         uint32_t n_skip = 0, n_unst = 0;
-        const float* lid = p.in.lid_dev_f;  // read where a lid node needs it
         const int inst = p.inst;
         // geometry of unit k of this warp
         auto geom = [&](int k) {
@@ -482,8 +482,8 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
             const int px = (g.sg << 5) + lane;  // pair within the row
             g.x = x0 + P * px;
             g.y = y0 + r;
-            g.hrow = (uint32_t)(TS::HALO_OFF + r * 16);  // this row's halo chunk
-            g.uo.own = (uint32_t)((r * X + P * px) * ES);
+            g.hrow = (uint32_t)(TS::HALO_OFF + (r << 4));  // this row's halo chunk
+            g.uo.own = (uint32_t)(((r << lgX) + P * px) * ES);
             g.uo.lft = (lane == 0) ? g.hrow + 4u * (uint32_t)(3 - g.sg) : g.uo.own - 4u;
             g.uo.rgt = (lane == 31 && g.sg == smask) ? g.hrow : g.uo.own + (uint32_t)(P * ES);
             // all 64 nodes of the unit are interior nodes of the lattice (the
@@ -532,8 +532,10 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
                     const bool second = x + 1 < nx;
                     // node (pair) on the lattice's outer ring: boundary rules apply
                     const bool edge = (y == 0) | (y == ny - 1) | (x == 0) | (x + P - 1 >= nx - 1);
+                    const int bc = p.in.bc;
                     if (edge && bc != BC_CAVITY) {
-                        const S* gb = src + off;
+                        const int64_t pitch = p.in.pitch, plane = p.in.plane;
+                        const S* gb = src + p.in.off;
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
                             const float2 g = global_pair<S>(gb + a * plane, pitch, nx, ny, bc, x,
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
                                 sts &= ~(3u << (2 * l));
                             } else if (lidn) {
 #pragma unroll
-                                for (int a = 0; a < Q; ++a) N::set_lane(o[a], l, lid[a]);
+                                for (int a = 0; a < Q; ++a) N::set_lane(o[a], l, p.in.lid_dev_f[a]);
                                 sts &= ~(3u << (2 * l));
                             }
                         }
@@ -618,8 +620,9 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
 template <typename S, int VARIANT>
 const void* pick_step_kernel_smem(int collision, size_t* smem_bytes) {
     constexpr int TN = smem_tile_nodes(sizeof(S) == 4 ? 1 : 2, VARIANT);  // 1: FP32 storage
-    constexpr int NS = VARIANT == 1 ? LBM_SMEM_STAGES_SMALL
-                     : VARIANT == 3 ? LBM_SMEM_STAGES_DEEP : LBM_SMEM_STAGES;
+    constexpr int NS = VARIANT == 1   ? LBM_SMEM_STAGES_SMALL
+                     : VARIANT == 3 ? (sizeof(S) == 2 ? LBM_SMEM_STAGES_DEEP2 : LBM_SMEM_STAGES_DEEP)
+                                    : LBM_SMEM_STAGES;
     constexpr int NT = smem_threads(VARIANT);
     using TS = SmemTile<S, TN, NS, NT>;
     *smem_bytes = TS::SMEM_BYTES;
