@@ -285,7 +285,9 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * nodes, two-stage ring; 4: deep ring, one 16-warp CTA per SM, 1920 / 960
  * nodes, four stages.  For kinds 1
  * to 4 the tile width is 64/128/256 nodes chosen per instance (at most
- * 32 tile nodes / colliding threads) and out[1], out[2] are 0; tiles go in and out of
+ * 32 tile nodes / colliding threads; of those, the one whose tiles cover
+ * the instance with the fewest padding nodes) and out[1], out[2] are 0;
+ * tiles go in and out of
  * shared memory by TMA).  Selection: the create-time
  * autotuner (median of three timed launches per candidate shape; the choice
  * is cached per device, lattice, types, rule, boundary and instance sizes

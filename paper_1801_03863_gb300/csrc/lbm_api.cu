@@ -82,12 +82,13 @@ std::vector<Shape> candidate_shapes(int lattice, int storage, int64_t max_nx, in
 }
 
 int64_t count_tiles(const std::vector<std::pair<int64_t, int64_t>>& dims, const Shape& s,
-                    int storage) {
+                    int storage, bool least_padding) {
     int64_t n = 0;
     if (s.kind >= 1) {
         for (auto& d : dims) {
             const int tn = smem_tile_nodes(storage, s.kind - 1);
-            const int64_t X = smem_tile_width(d.first, tn, smem_threads(s.kind - 1));
+            const int64_t X = smem_tile_width(d.first, d.second, tn, smem_threads(s.kind - 1),
+                                              least_padding);
             const int64_t R = tn / X;
             n += ((d.first + X - 1) / X) * ((d.second + R - 1) / R);
         }
@@ -138,10 +139,10 @@ Layout make_layout(int lattice, int storage, const std::vector<std::pair<int64_t
         const int64_t chunks = (d.first + 1) / 2;
         bound += chunks * d.second / 128 + chunks / 4 + d.second + 1;
     }
-    L.max_tiles = std::max({bound, count_tiles(dims, Shape{2, 0, 0, 1}, storage),
-                            count_tiles(dims, Shape{2, 0, 0, 2}, storage),
-                            count_tiles(dims, Shape{2, 0, 0, 3}, storage),
-                            count_tiles(dims, Shape{2, 0, 0, 4}, storage)});
+    L.max_tiles = bound;
+    for (int kind = 1; kind <= 4; ++kind)
+        for (bool lp : {false, true})
+            L.max_tiles = std::max(L.max_tiles, count_tiles(dims, Shape{2, 0, 0, kind}, storage, lp));
     return L;
 }
 
@@ -264,7 +265,8 @@ std::vector<TileDesc> build_tiles(const lbm_ctx* ctx, const Shape& s) {
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
             const int tn = smem_tile_nodes(ctx->storage, s.kind - 1);
-            const int X = smem_tile_width(in.nx, tn, smem_threads(s.kind - 1));
+            const int X = smem_tile_width(in.nx, in.ny, tn, smem_threads(s.kind - 1),
+                                          smem_least_padding(ctx->collision));
             const int R = tn / X;
             for (int64_t y0 = 0; y0 < in.ny; y0 += R)
                 for (int64_t x0 = 0; x0 < in.nx; x0 += X)
@@ -367,7 +369,8 @@ int build_tensor_maps(lbm_ctx* ctx, int variant) {
         const bool halo = (m & 1) != 0;
         for (int i = 0; i < ctx->count; ++i) {
             const InstDesc& in = ctx->layout.inst[i];
-            const int X = smem_tile_width(in.nx, tile_nodes, smem_threads(variant));
+            const int X = smem_tile_width(in.nx, in.ny, tile_nodes, smem_threads(variant),
+                                          smem_least_padding(ctx->collision));
             const int R = tile_nodes / X;
             void* base = ctx->buf[b] + (size_t)in.off * es;
             cuuint64_t dims[3] = {(cuuint64_t)in.nx, (cuuint64_t)in.ny, 9};

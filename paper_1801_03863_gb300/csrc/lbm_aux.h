@@ -102,13 +102,35 @@ constexpr int smem_units(int storage, int variant) {
 constexpr int smem_tile_nodes(int storage, int variant) {
     return 64 * smem_units(storage, variant) * (smem_threads(variant) / 32);
 }
-// Tile width: 64, 128 or 256 nodes by the instance width, at most
-// 32 tile_nodes / threads, so that each warp's units (tile_nodes /
-// (2 threads) units of 64 nodes) cover whole tile rows.
-inline int smem_tile_width(int64_t nx, int tile_nodes, int threads) {
-    int w = nx >= 256 ? 256 : (nx >= 128 ? 128 : 64);
-    while (w > 64 && (int64_t)w * threads > 32LL * tile_nodes) w /= 2;
-    return w;
+// Tile width X of an nx x ny instance: 64, 128 or 256 nodes (at most nx
+// unless 64), at most 32 tile_nodes / threads so that each warp's units
+// (tile_nodes / (2 threads) units of 64 nodes) cover whole tile rows.  Of
+// those, the widest (fewest halo columns and tile copies per node: what
+// the bandwidth-bound rules want), or with least_padding the one whose
+// tiles (X by tile_nodes / X rows) cover the instance with the fewest
+// padding nodes (what arithmetic-bound rules want: a padding lane collides
+// for nothing); ties go to the wider tile.
+inline int smem_tile_width(int64_t nx, int64_t ny, int tile_nodes, int threads,
+                           bool least_padding) {
+    int best = 64;
+    int64_t best_cells = -1;
+    for (int w = 256; w >= 64; w /= 2) {
+        if ((int64_t)w * threads > 32LL * tile_nodes) continue;
+        if (w > 64 && nx < w) continue;
+        if (!least_padding) return w;
+        const int64_t R = tile_nodes / w;
+        const int64_t cells = ((nx + w - 1) / w) * w * (((ny + R - 1) / R) * R);
+        if (best_cells < 0 || cells < best_cells) {
+            best_cells = cells;
+            best = w;
+        }
+    }
+    return best;
+}
+// The MinxEnt rules are arithmetic-bound on the TMA kernel, the others
+// bandwidth-bound.
+constexpr bool smem_least_padding(int collision) {
+    return collision == COLL_MINXENT4 || collision == COLL_MINXENT2;
 }
 
 }  // namespace lbm
