@@ -254,20 +254,25 @@ __device__ void node_state_f32(const S* base, const InstDesc& in, int x, int y, 
 // few of its nodes of a row together, adding them in order), and the block
 // reduces
 // its threads in a fixed tree into partials[(i*CONS_PARTIALS + b)*3 + c].
-// The order is fixed by the instance alone.  The sums run in FP64, except
-// for FP16 storage, where they are exact integers: every FP16 value is a
-// multiple of 2^-24 below 2^16 in magnitude, so 2^24 d is an integer below
-// 2^40, and a thread's nodes add exactly in 64-bit integers, converted to
-// FP64 once (a node with a non-finite value takes the FP64 path, so that it
-// propagates); nodes whose values are all below 8 in magnitude, which is
-// every node of a physical state, sum in 32-bit integers first, without
-// 64-bit conversions.  Interior nodes pull with plain shifted
+// The order is fixed by the instance alone.  FP64 storage sums in FP64.
+// FP32 and BF16 storage sum in compensated FP32 pairs (Knuth's two-sum;
+// about twice FP32's precision, converted to FP64 once per thread), which
+// spares the slow FP64 pipe.  FP16 storage sums exactly in integers: every
+// FP16 value is a multiple of 2^-24 below 2^16 in magnitude, so 2^24 d is an
+// integer below 2^40, and a thread's nodes add exactly in 64-bit integers,
+// converted to FP64 once; nodes whose values are all below 8 in magnitude,
+// which is every node of a physical state, sum in 32-bit integers first,
+// without 64-bit conversions.  A node with a non-finite value takes the
+// FP64 path, so that it propagates.  Interior nodes pull with plain shifted
 // loads; the outer ring applies the boundary rules.
 template <class Lat, typename S>
 __global__ void __launch_bounds__(CONS_THREADS, CONS_MIN_BLOCKS)
 cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool pulled,
                     double* partials) {
-    using V = typename std::conditional<sizeof(S) == 2, float, double>::type;
+    using V = typename std::conditional<sizeof(S) == 8, double, float>::type;
+    // FP32 and BF16 values sum in FP32 pairs (compensated: each addition's
+    // rounding error is kept, so a pair carries about twice FP32's precision)
+    constexpr bool DF = std::is_same<S, float>::value || std::is_same<S, __nv_bfloat16>::value;
     // nodes x, x + T, ..., x + (K - 1) T of a row (T = CONS_THREADS) whose
     // loads a thread issues together before it adds them in order
     constexpr int K = sizeof(S) == 8 ? 2 : 4;
@@ -278,6 +283,15 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
     const S* base = src + in.off;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     long long i0 = 0, i1 = 0, i2 = 0;  // FP16: exact sums in units of 2^-24
+    float h0 = 0.f, c0 = 0.f, h1 = 0.f, c1 = 0.f, h2 = 0.f, c2 = 0.f;  // FP32 / BF16: (sum, error)
+    // h + v = s + e exactly (Knuth's two-sum); the error joins the running c
+    auto add2 = [](float& h, float& c, float v) {
+        const float sum = __fadd_rn(h, v);
+        const float bv = __fsub_rn(sum, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bv)), __fsub_rn(v, bv));
+        h = sum;
+        c = __fadd_rn(c, e);
+    };
     for (int y = it.y; y < ny; y += P) {
         const bool yint = Lat::Q == 3 || (y >= 1 && y <= ny - 2);
         for (int x0 = threadIdx.x; x0 < nx; x0 += K * CONS_THREADS) {
@@ -303,10 +317,10 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
             if ((plain >> k) & 1u) {
 #pragma unroll
                 for (int a = 0; a < Lat::Q; ++a) {
-                    if constexpr (sizeof(S) == 2) d[a] = Store<S>::to_f32(raw[k][a]);
+                    if constexpr (sizeof(S) != 8) d[a] = Store<S>::to_f32(raw[k][a]);
                     else d[a] = Store<S>::to_f64(raw[k][a]);
                 }
-            } else if constexpr (sizeof(S) == 2) {
+            } else if constexpr (sizeof(S) != 8) {
                 node_state_f32<Lat, S>(src, in, x, y, pulled, d);
             } else {
                 node_state<Lat, S>(src, in, x, y, pulled, d);
@@ -350,6 +364,20 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
                     }
                 }
             }
+            if constexpr (DF) {
+                bool finite = true;
+#pragma unroll
+                for (int a = 0; a < Lat::Q; ++a) finite = finite && (fabsf(d[a]) <= 3.4028235e38f);
+                if (finite) {
+#pragma unroll
+                    for (int a = 0; a < Lat::Q; ++a) {
+                        add2(h0, c0, d[a]);
+                        if (Lat::vx(a) != 0) add2(h1, c1, Lat::vx(a) > 0 ? d[a] : -d[a]);
+                        if (Lat::vy(a) != 0) add2(h2, c2, Lat::vy(a) > 0 ? d[a] : -d[a]);
+                    }
+                    exact = true;
+                }
+            }
             if (!exact) {
 #pragma unroll
                 for (int a = 0; a < Lat::Q; ++a) {
@@ -369,6 +397,11 @@ cons_partial_kernel(const S* src, const InstDesc* insts, const int2* items, bool
         s0 += (double)i0 * inv;
         s1 += (double)i1 * inv;
         s2 += (double)i2 * inv;
+    }
+    if constexpr (DF) {
+        s0 += (double)h0 + (double)c0;
+        s1 += (double)h1 + (double)c1;
+        s2 += (double)h2 + (double)c2;
     }
     sh[0][threadIdx.x] = s0;
     sh[1][threadIdx.x] = s1;
