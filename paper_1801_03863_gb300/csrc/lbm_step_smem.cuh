@@ -213,19 +213,19 @@ template <typename S, int VX>
 __device__ __forceinline__ float2 smem_pair(const unsigned char* pl, const UnitOffs& u,
                                             uint32_t* own_word = nullptr) {
     if constexpr (sizeof(S) == 2) {
+        using S2 = typename std::conditional<std::is_same<S, __half>::value, __half2,
+                                             __nv_bfloat162>::type;
         const uint32_t w0 = *reinterpret_cast<const uint32_t*>(pl + u.own);
         if (own_word) *own_word = w0;
-        uint32_t v;
-        if constexpr (VX == 0) v = w0;
+        // each half converted straight from the word that holds it (the
+        // conversion picks either half of a register; no byte permute)
+        auto lo = [](uint32_t w) { return __low2float(*reinterpret_cast<const S2*>(&w)); };
+        auto hi = [](uint32_t w) { return __high2float(*reinterpret_cast<const S2*>(&w)); };
+        if constexpr (VX == 0) return make_float2(lo(w0), hi(w0));
         else if constexpr (VX == 1)
-            v = __byte_perm(*reinterpret_cast<const uint32_t*>(pl + u.lft), w0, 0x5432);
+            return make_float2(hi(*reinterpret_cast<const uint32_t*>(pl + u.lft)), lo(w0));
         else
-            v = __byte_perm(w0, *reinterpret_cast<const uint32_t*>(pl + u.rgt), 0x5432);
-        if constexpr (std::is_same<S, __half>::value) {
-            return __half22float2(*reinterpret_cast<const __half2*>(&v));
-        } else {
-            return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
-        }
+            return make_float2(hi(w0), lo(*reinterpret_cast<const uint32_t*>(pl + u.rgt)));
     } else {
         if constexpr (VX == 0) return *reinterpret_cast<const float2*>(pl + u.own);
         else if constexpr (VX == 1)
@@ -302,6 +302,9 @@ __device__ __forceinline__ float2 global_pair(const S* base, int64_t pitch, int 
     return make_float2(to_compute<float, S>(row[xa]), to_compute<float, S>(row[xb]));
 }
 
+#ifndef LBM_UNIT_UNROLL
+#define LBM_UNIT_UNROLL 1  // 0: a warp takes its units of a tile in a rolled loop
+#endif
 #ifndef LBM_SMEM_MINBLOCKS
 #define LBM_SMEM_MINBLOCKS 2  // resident CTAs per SM the register budget aims at
 #endif
@@ -579,7 +582,6 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
                 for (int a = 0; a < Q; ++a)
                     smem_store_pair<S>(sb + a * PB + uo.own, o[a].v.x, o[a].v.y);
             };
-#pragma unroll 1
         auto single = [&](const UnitGeom& g) {
             if constexpr (FAST) {
                 if (g.interior) unit(std::true_type{}, g);
@@ -588,8 +590,13 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
                 unit(std::false_type{}, g);
             }
         };
-        // one unit at a time (unrolling, or two units collided together,
+        // one unit at a time, the loop unrolled (two units collided together
         // measured slower: registers)
+#if LBM_UNIT_UNROLL
+#pragma unroll
+#else
+#pragma unroll 1
+#endif
         for (int k = 0; k < TS::UNITS; ++k) single(geom(k));
         if (n_skip | n_unst) {
             atomicAdd(args.status + 2 * inst + 0, (unsigned long long)n_skip);
