@@ -126,8 +126,10 @@ class Workload:
         self.lattice, self.bc = "d2q9", "cavity"
         self.u_lid = None
         self.member_ids = [0]
+        self.total_members = 1  # members over all ranks (single-instance runs: replicas)
         if name == "ensemble64":
             per = members_per_gpu or MEMBERS_PER_GPU
+            self.total_members = per * world
             members = wl.cavity_ensemble(count=per * world, seed=0)
             mine = partition([m.side * m.side for m in members], world)[rank]
             self.member_ids = list(mine)
@@ -151,7 +153,8 @@ class Workload:
             self.rho, self.ux, self.uy = r.ravel(), x.ravel(), y.ravel()
         elif name == "tubes4096":
             self.lattice, self.bc = "d1q3", "zero_gradient"
-            members = wl.tube_ensemble(count=(members_per_gpu or 4096) * world, seed=1)
+            self.total_members = (members_per_gpu or 4096) * world
+            members = wl.tube_ensemble(count=self.total_members, seed=1)
             mine = partition([m.n for m in members], world)[rank]
             self.member_ids = list(mine)
             self.dims = [(members[i].n, 1) for i in mine]
@@ -456,6 +459,16 @@ def run_ours(args, dist):
                           f"{args.collision.upper()}",
                 "avg_launch_ms": launch_ms}
 
+    # the sharded path's one collective: every rank gets every member's
+    # conservation totals (ensembles; single-instance runs are replicas)
+    totals = None
+    if wk.total_members > 1 or dist.world == 1:
+        from paper_1801_03863_gb300.partition import gather_totals
+        table = gather_totals(cons.view(-1, 3).cpu().numpy(), wk.member_ids, wk.total_members,
+                              dist.pg)
+        totals = {"members": int(table.shape[0]), "sum_rho": float(table[:, 0].sum()),
+                  "sum_rho_u": [float(table[:, 1].sum()), float(table[:, 2].sum())]}
+
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -465,6 +478,7 @@ def run_ours(args, dist):
         "gpu_launches": args.steps + 2 * len(chunks),
         "clocks": sampler.summary(),
         "status": st,
+        "totals": totals,
     }
 
     if not args.no_extras and dist.rank == 0:

@@ -34,3 +34,27 @@ def imbalance(costs: Sequence[float], shares: list[list[int]]) -> float:
     loads = [sum(float(costs[i]) for i in s) for s in shares]
     mean = sum(loads) / len(loads)
     return max(loads) / mean if mean > 0 else 1.0
+
+
+def gather_totals(local_totals, member_ids: Sequence[int], count: int, dist=None):
+    """All ranks' per-member conservation totals as one (count, 3) FP64 table.
+
+    local_totals: this rank's (len(member_ids), 3) totals (sum rho, sum rho u_x,
+    sum rho u_y), row j for global member member_ids[j].  Every rank fills its
+    own rows of a zero table and the tables are summed across ranks (one
+    all-reduce): each row has exactly one nonzero contribution, and x + 0 is
+    exact, so the result is bitwise what a single rank would report.
+    dist: torch.distributed (initialised) or None for one rank.
+    """
+    import numpy as np
+    import torch
+
+    table = np.zeros((count, 3), dtype=np.float64)
+    loc = np.asarray(local_totals, dtype=np.float64).reshape(len(member_ids), 3)
+    table[list(member_ids)] = loc
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return table
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.from_numpy(table).to(dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()

@@ -126,10 +126,14 @@ def _share_main(rank, world, port, q, name, per_gpu, steps):
                        "WORLD_SIZE": str(world), "RANK": str(rank), "LOCAL_RANK": str(rank),
                        "OMP_NUM_THREADS": "2"})
     import bench
+    from paper_1801_03863_gb300.partition import gather_totals
     d = bench.Dist()
     res = _share_results(name, rank, world, per_gpu, steps)
+    ids = sorted(res)
+    # the one collective of the sharded path: every rank gets all totals
+    table = gather_totals([res[m][0] for m in ids], ids, per_gpu * world, d.pg)
     d.barrier()
-    q.put((rank, res))
+    q.put((rank, {"members": res, "table": table}))
     d.close()
 
 
@@ -139,13 +143,18 @@ def test_ranks_advance_their_share_like_one_rank(name, per_gpu, steps):
     res = _spawn(world, _share_main, (name, per_gpu, steps))
     got = {}
     for _, part in res:
-        assert not set(part) & set(got)  # no member on two ranks
-        got.update(part)
+        assert not set(part["members"]) & set(got)  # no member on two ranks
+        got.update(part["members"])
     want = _share_results(name, 0, 1, per_gpu * world, steps)
     assert sorted(got) == sorted(want) == list(range(per_gpu * world))
     for mid in want:
         assert np.array_equal(got[mid][0], want[mid][0]), mid
         assert np.array_equal(got[mid][1], want[mid][1]), mid
+    # the gathered totals table is the same on every rank and equals the
+    # one-rank totals bit for bit
+    want_table = np.array([want[m][0] for m in range(per_gpu * world)])
+    for _, part in res:
+        assert np.array_equal(part["table"], want_table)
 
 
 # ----------------------------------------------------------------------------
