@@ -448,11 +448,9 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
         return;
     }
 
-    // Each warp collides its units of a tile, then its lane 0 arrives on the
-    // stage's empty barrier and counts itself done; the last warp to finish
-    // the tile writes it out and refills the stage with tile j + NS at once
-    // (after TMA has read the stores' sources), so the copies of the next
-    // tiles start as soon as a stage is free, whichever warp frees it.
+    // Each colliding warp collides its units of a tile, then its lane 0
+    // arrives on the stage's empty barrier; the copy warp takes the tile
+    // from there.
     bool fail = false;
     int j = 0;
     for (; j < ntl && !fail; ++j) {
