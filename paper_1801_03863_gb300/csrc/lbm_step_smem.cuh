@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(NTHREADS + 32, NTHREADS + 32 >= 512 ? 1 : LBM_
                 uint32_t sts;
                 if constexpr (INTERIOR) {
                     sts = Collide<D2Q9, COLL, CT, ES>::run(d, rho0v, rates, o);
-                    if (sts) {  // rare: some lane skipped its Newton step or is unstable
+                    if (__builtin_expect(sts != 0u, 0)) {  // rare: a lane skipped its Newton step or is unstable
                         n_skip += __popc(sts & (ST_NEWTON_SKIPPED * 5u));
                         n_unst += __popc(sts & (ST_UNSTABLE * 5u));
                     }
