@@ -282,8 +282,8 @@ def test_conservation_reduced_storage_matches_state_sums(storage, bc):
     back as FP64 populations, right after a load (stored f(t_n)) and after
     steps (the pulled f(t_n)), for an instance taller than the 64 partial
     rows of the reduction and one shorter.  Every storage type agrees to
-    FP64 rounding: FP32 and BF16 node sums run in FP64, FP16 node sums are
-    exact integers of 2^-24 units (no FP32 rounding anywhere)."""
+    FP64 rounding: FP32 and BF16 values sum in compensated FP32 pairs, FP16
+    node sums are exact integers of 2^-24 units (no FP32 rounding anywhere)."""
     dims = [(150, 133), (37, 20)]
     f0 = np.concatenate([wl.random_populations(9, ny, nx, eps=0.2, seed=11 + i).ravel()
                          for i, (nx, ny) in enumerate(dims)])
@@ -300,6 +300,28 @@ def test_conservation_reduced_storage_matches_state_sums(storage, bc):
             k += 9 * nx * ny
             want = np.array([fi.sum(), (_VX[:, None] * fi).sum(), (_VY[:, None] * fi).sum()])
             assert np.abs(cons[i] - want).max() <= 2e-12 * want[0], (storage, bc, i)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_conservation_propagates_non_finite_values(storage):
+    """A NaN or an infinity in an instance's state makes that instance's
+    totals NaN / infinite (the reduction's fast paths hand such nodes to the
+    FP64 path); the other instances' totals stay finite and exact."""
+    dims = [(40, 30), (33, 21), (25, 25)]
+    f0 = np.concatenate([wl.random_populations(9, ny, nx, eps=0.05, seed=31 + i).ravel()
+                         for i, (nx, ny) in enumerate(dims)])
+    base = [0, 9 * 40 * 30, 9 * (40 * 30 + 33 * 21)]
+    f0[base[0] + 5 * 40 * 30 + 7] = np.nan      # instance 0: a NaN
+    f0[base[1] + 2 * 33 * 21 + 100] = np.inf    # instance 1: +inf, pulled along +y
+    with lbm.Lattice("d2q9", dims, 0.02, "periodic", compute="f32", storage=storage) as lat:
+        lat.set_populations(f0)
+        cons = lat.conservation()
+        f = lat.populations()
+    assert np.isnan(cons[0, 0])
+    assert np.isinf(cons[1, 0]) and cons[1, 0] > 0 and np.isinf(cons[1, 2])
+    fi = f[base[2]:].reshape(9, 25 * 25)
+    want = np.array([fi.sum(), (_VX[:, None] * fi).sum(), (_VY[:, None] * fi).sum()])
+    assert np.all(np.isfinite(cons[2])) and np.abs(cons[2] - want).max() <= 2e-12 * want[0]
 
 
 def test_conservation_periodic_is_exact_and_reproducible():
