@@ -283,10 +283,11 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * 2-byte storage or 896 for FP32, two-stage ring; 2: small tiles, 8-warp
  * CTAs, 896 / 448 nodes, three-stage ring; 3: 10-warp CTAs, 2304 / 1152
  * nodes, two-stage ring; 4: deep ring, one 16-warp CTA per SM, 1920 / 960
- * nodes, four stages.  For kinds 1
+ * nodes, five stages (four for FP32 storage).  For kinds 1
  * to 4 the tile width is 64/128/256 nodes chosen per instance (at most
- * 32 tile nodes / colliding threads; of those, the one whose tiles cover
- * the instance with the fewest padding nodes) and out[1], out[2] are 0;
+ * 32 tile nodes / colliding threads; of those, for the MinxEnt rules the
+ * one whose tiles cover the instance with the fewest padding nodes, for the
+ * others the widest) and out[1], out[2] are 0;
  * tiles go in and out of
  * shared memory by TMA).  Selection: the create-time
  * autotuner (each candidate shape timed over back-to-back launches, the

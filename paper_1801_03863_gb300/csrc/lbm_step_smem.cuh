@@ -8,7 +8,7 @@
 //    or 256, chosen per instance) by R = TILE_NODES / X rows.  Four
 //    geometries are compiled (smem_tile_nodes): 8-warp CTAs with large or
 //    small tiles on two- or three-stage rings, 10-warp CTAs, and one
-//    16-warp CTA per SM on a four-stage ring; the autotuner picks per
+//    16-warp CTA per SM on a five-stage ring (four for FP32 storage); the autotuner picks per
 //    context.
 //  * Each instance's populations are described to TMA as a 3-D tensor
 //    (x < nx, row, plane).  Every copy starts at an x that is a multiple of
