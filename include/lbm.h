@@ -291,7 +291,8 @@ int lbm_status_instance(lbm_ctx* ctx, int32_t instance, int64_t* counters);
  * tiles go in and out of
  * shared memory by TMA).  Selection: the create-time
  * autotuner (each candidate shape timed over back-to-back launches, the
- * candidates within 5 % of the fastest timed a second time; the choice
+ * candidates within 5 % of the fastest timed again as a captured graph,
+ * which decides; the choice
  * is cached per device, lattice, types, rule, boundary and instance sizes
  * for the life of the process, and in the text file named by the
  * environment variable LBM_AUTOTUNE_CACHE when set, which later processes
