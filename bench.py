@@ -263,9 +263,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_node(storage: str):
+def traffic_per_node(storage: str, kind: str):
     """DRAM bytes per node of the step kernel from the committed ncu summary,
-    or None when the kernel changed since the counters were taken."""
+    or None when the kernel changed since the counters were taken or the
+    counters were taken on another launch shape."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
@@ -274,7 +275,7 @@ def traffic_per_node(storage: str):
     except ValueError:
         return None
     e = d.get(storage)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash() or e.get("kind") != kind:
         return None
     return float(e["dram_bytes_per_node"])
 
@@ -448,8 +449,8 @@ def run_ours(args, dist):
     bpl = wk.bytes_per_lu(args.storage)
     launch_ms = step_ms / args.steps
     achieved = wk.nodes * bpl / (launch_ms * 1e-3) / 1e9
-    tpn = traffic_per_node(f"{wk.name}:{args.storage}")
     shape = lat.launch_shape()
+    tpn = traffic_per_node(f"{wk.name}:{args.collision}:{args.storage}", shape["kind"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tpn is None else tpn * wk.nodes,
