@@ -229,7 +229,7 @@ def _dual_minimiser(orc, f, tau, nfree):
         return phi @ p - target
 
     sol = optimize.root(resid, np.zeros(len(rows)), method="hybr", tol=1e-15)
-    # hybr reports "no further improvement" once at machine precision: judge
+    # hybr reports "no further improvement" once at machine precision: assess
     # convergence by the residual itself
     assert np.max(np.abs(resid(sol.x))) < 1e-14
     return rho * w * np.exp(sol.x @ phi)
